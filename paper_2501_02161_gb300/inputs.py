@@ -1,0 +1,290 @@
+"""Seeded synthetic lattices: node flags, design field gamma and boundary values.
+
+This module only builds inputs. It holds none of the method's arithmetic (no
+equilibrium, collision, boundary scheme or adjoint), so both the CUDA path and
+the FP64 oracle can take their inputs from it.
+
+Flag byte per node (the layout the C-ABI documents):
+  bits 0-2  node type   0 FLUID, 1 WALL (full-way bounce-back), 2 VEL (Zou-He
+            velocity inlet, Eq. 7), 3 PRES (Zou-He fixed-density outlet, Eq. 8)
+  bits 3-5  inward normal of an open boundary or heated wall:
+            0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
+  bit 6     HEAT  wall node that injects a heat flux towards its normal
+  bit 7     reserved (0)
+
+Boundary values, 4 numbers per node (only read at VEL / PRES nodes):
+  VEL:  (ux, uy, uz, T_in)      PRES: (rho_out, 0, 0, 0)
+
+Node linear index n = x + nx*(y + ny*z); arrays are returned flat in that order.
+
+The paper's geometries (pipe bend, Fig. 1 and Fig. 9; microchannel heat sink,
+Fig. 15) exist only as schematics, so these generators stand in for them with
+the sizes of the workloads they are used for.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+FLUID, WALL, VEL, PRES = 0, 1, 2, 3
+NORMAL_CODES = {(1, 0, 0): 0, (-1, 0, 0): 1, (0, 1, 0): 2, (0, -1, 0): 3,
+                (0, 0, 1): 4, (0, 0, -1): 5}
+HEAT_BIT = 1 << 6
+
+D2Q9, D3Q19 = 0, 1
+GAMMA_EQ12, GAMMA_LINEAR = 0, 1
+
+
+def make_flag(kind: int, normal=(1, 0, 0), heat: bool = False) -> int:
+    return (kind & 7) | (NORMAL_CODES[tuple(normal)] << 3) | (HEAT_BIT if heat else 0)
+
+
+@dataclass
+class Lattice:
+    """A synthetic problem: geometry + design field + physical parameters."""
+    name: str
+    stencil: int
+    nx: int
+    ny: int
+    nz: int
+    flags: np.ndarray          # uint8[N]
+    gamma: np.ndarray          # float64[N]
+    bcval: np.ndarray          # float64[N*4]
+    tau: float
+    rho0: float = 1.0
+    gamma_model: int = GAMMA_EQ12
+    thermal: bool = False
+    kappa_f: float = 0.0       # fluid thermal diffusivity (lattice units)
+    k_ratio: float = 1.0       # solid / fluid conductivity ratio
+    q_flux: float = 0.0        # heat added per step at each HEAT wall node
+    T0: float = 0.0            # initial temperature
+    w_pin: float = 1.0         # objective weight of mean inlet pressure
+    w_tmean: float = 0.0       # objective weight of mean temperature
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def dims(self):
+        return (self.nx, self.ny, self.nz)
+
+
+def idx(nx, ny, x, y, z=0):
+    return x + nx * (y + ny * z)
+
+
+# --------------------------------------------------------------------------
+# seeded random fields
+# --------------------------------------------------------------------------
+
+def uniform_noise(n: int, seed: int) -> np.ndarray:
+    """U[0,1) per node from numpy's PCG64 with the given seed."""
+    return np.random.default_rng(seed).random(n)
+
+
+def _gauss_kernel(sigma: float) -> np.ndarray:
+    r = int(math.ceil(3.0 * sigma))
+    t = np.arange(-r, r + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (t / sigma) ** 2)
+    return k / k.sum()
+
+
+def gaussian_filter_nearest(a: np.ndarray, sigma: float) -> np.ndarray:
+    """Separable Gaussian blur truncated at 3 sigma, edges clamped (nearest)."""
+    k = _gauss_kernel(sigma)
+    r = (len(k) - 1) // 2
+    out = a.astype(np.float64)
+    for ax in range(out.ndim):
+        if out.shape[ax] == 1:
+            continue
+        pad = [(0, 0)] * out.ndim
+        pad[ax] = (r, r)
+        p = np.pad(out, pad, mode="edge")
+        acc = np.zeros_like(out)
+        for j, kj in enumerate(k):
+            sl = [slice(None)] * out.ndim
+            sl[ax] = slice(j, j + out.shape[ax])
+            acc += kj * p[tuple(sl)]
+        out = acc
+    return out
+
+
+def filtered_design(shape_zyx, seed: int, sigma: float = 3.0,
+                    mean: float = 0.5, std: float = 0.25) -> np.ndarray:
+    """Gaussian-filtered uniform noise, affinely rescaled, clipped to [0,1].
+
+    Filtered U[0,1) noise has a standard deviation of about 0.01 at sigma=3,
+    so clipping alone would leave a near-uniform 0.5 field; the rescale to
+    (mean, std) keeps the spatial structure and gives solid-like and fluid-like
+    regions.
+    """
+    n = int(np.prod(shape_zyx))
+    g = gaussian_filter_nearest(uniform_noise(n, seed).reshape(shape_zyx), sigma)
+    s = g.std()
+    g = (g - g.mean()) / (s if s > 0 else 1.0) * std + mean
+    return np.clip(g, 0.0, 1.0)
+
+
+# --------------------------------------------------------------------------
+# inlet profiles (prescribed boundary data)
+# --------------------------------------------------------------------------
+
+def parabola(j: int, w: int) -> float:
+    s = (j + 0.5) / w
+    return 4.0 * s * (1.0 - s)
+
+
+def tau_from_re(re: float, umax: float, width: float) -> float:
+    """Re := u_max * W / nu with nu = (tau - 1/2)/3 (Eq. 3)."""
+    nu = umax * width / re
+    return 0.5 + 3.0 * nu
+
+
+# --------------------------------------------------------------------------
+# geometries
+# --------------------------------------------------------------------------
+
+def pipe_bend_2d(nx: int = 64, ny: int = 64, width: int = 16, umax: float = 0.05,
+                 tau: float = 0.6, gamma_value: float = 0.5,
+                 gamma_model: int = GAMMA_EQ12) -> Lattice:
+    """2D pipe bend (Fig. 1): inlet on the left face, outlet on the top face.
+
+    Walls on the outer ring; inlet x=0, y in [ny/8, ny/8+W) with a parabolic
+    Zou-He velocity profile; outlet y=ny-1, x in [5nx/8, 5nx/8+W) at rho=1.
+    gamma is uniform on non-wall nodes.
+    """
+    flags = np.zeros((ny, nx), np.uint8)
+    gam = np.full((ny, nx), gamma_value)
+    bc = np.zeros((ny, nx, 4))
+    flags[0, :] = flags[-1, :] = WALL
+    flags[:, 0] = flags[:, -1] = WALL
+    y0 = ny // 8
+    x0 = (5 * nx) // 8
+    for j in range(width):
+        y = y0 + j
+        flags[y, 0] = make_flag(VEL, (1, 0, 0))
+        bc[y, 0, :] = (umax * parabola(j, width), 0.0, 0.0, 0.0)
+        x = x0 + j
+        flags[ny - 1, x] = make_flag(PRES, (0, -1, 0))
+        bc[ny - 1, x, :] = (1.0, 0.0, 0.0, 0.0)
+    gam[(flags & 7) == WALL] = 0.0
+    lat = Lattice("pipe_bend_2d", D2Q9, nx, ny, 1, flags.ravel(), gam.ravel(),
+                  bc.ravel(), tau=tau, gamma_model=gamma_model)
+    lat.meta.update(width=width, umax=umax,
+                    re=umax * width / ((tau - 0.5) / 3.0))
+    return lat
+
+
+def pipe_bend_3d(n: int = 64, width: int | None = None, umax: float = 0.05,
+                 re: float = 100.0, seed: int = 1, sigma: float = 3.0,
+                 gamma_uniform: float | None = None, ny: int | None = None,
+                 nz: int | None = None, gamma_model: int = GAMMA_EQ12) -> Lattice:
+    """3D pipe bend (Fig. 9): square inlet on x=0, square outlet on y=ny-1.
+
+    Inlet x=0, y in [ny/8, ny/8+W), z centred; outlet y=ny-1, x in
+    [5nx/8, 5nx/8+W), z centred; W = n/4 by default (16 at 64^3).  gamma is the
+    filtered random design on interior nodes and 1 on the openings.
+    """
+    nx = n
+    ny = ny or n
+    nz = nz or n
+    w = width or max(2, n // 4)
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    bc = np.zeros((nz, ny, nx, 4))
+    flags[0, :, :] = flags[-1, :, :] = WALL
+    flags[:, 0, :] = flags[:, -1, :] = WALL
+    flags[:, :, 0] = flags[:, :, -1] = WALL
+    y0 = ny // 8
+    x0 = (5 * nx) // 8
+    z0 = nz // 2 - w // 2
+    for a in range(w):
+        for b in range(w):
+            prof = 16.0 * umax * (parabola(a, w) / 4.0) * (parabola(b, w) / 4.0)
+            flags[z0 + b, y0 + a, 0] = make_flag(VEL, (1, 0, 0))
+            bc[z0 + b, y0 + a, 0, :] = (prof, 0.0, 0.0, 0.0)
+            flags[z0 + b, ny - 1, x0 + a] = make_flag(PRES, (0, -1, 0))
+            bc[z0 + b, ny - 1, x0 + a, :] = (1.0, 0.0, 0.0, 0.0)
+    if gamma_uniform is not None:
+        gam = np.full((nz, ny, nx), float(gamma_uniform))
+    else:
+        gam = filtered_design((nz, ny, nx), seed, sigma)
+    kind = flags & 7
+    gam[(kind == VEL) | (kind == PRES)] = 1.0
+    gam[kind == WALL] = 0.0
+    tau = tau_from_re(re, umax, w)
+    lat = Lattice(f"pipe_bend_3d_{nx}x{ny}x{nz}", D3Q19, nx, ny, nz,
+                  flags.ravel(), gam.ravel(), bc.ravel(), tau=tau,
+                  gamma_model=gamma_model)
+    lat.meta.update(width=w, umax=umax, re=re, seed=seed)
+    return lat
+
+
+def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
+              re: float = 50.0, pr: float = 7.0, k_ratio: float = 100.0,
+              q_flux: float = 1e-3, seed: int = 4, sigma: float = 3.0,
+              w_pin: float = 1.0, w_tmean: float = 1.0,
+              gamma_uniform: float | None = None,
+              gamma_model: int = GAMMA_EQ12) -> Lattice:
+    """Microchannel heat sink (Fig. 15), flow along +x through a design block.
+
+    Inlet face x=0 and outlet face x=nx-1 over the interior cross-section
+    (velocity inlet with a product parabola and T=0; fixed-density outlet).
+    Walls on y=0, y=ny-1, z=0, z=nz-1; the z=0 wall under the interior is
+    heated with q_flux per node and step.  Re uses the smaller inlet side.
+    """
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    bc = np.zeros((nz, ny, nx, 4))
+    flags[0, :, :] = flags[-1, :, :] = WALL
+    flags[:, 0, :] = flags[:, -1, :] = WALL
+    wy, wz = ny - 2, nz - 2
+    for z in range(1, nz - 1):
+        for y in range(1, ny - 1):
+            prof = 16.0 * umax * (parabola(y - 1, wy) / 4.0) * (parabola(z - 1, wz) / 4.0)
+            flags[z, y, 0] = make_flag(VEL, (1, 0, 0))
+            bc[z, y, 0, :] = (prof, 0.0, 0.0, 0.0)
+            flags[z, y, nx - 1] = make_flag(PRES, (-1, 0, 0))
+            bc[z, y, nx - 1, :] = (1.0, 0.0, 0.0, 0.0)
+    heat = make_flag(WALL, (0, 0, 1), heat=True)
+    flags[0, 1:ny - 1, 1:nx - 1] = heat
+    if gamma_uniform is not None:
+        gam = np.full((nz, ny, nx), float(gamma_uniform))
+    else:
+        gam = filtered_design((nz, ny, nx), seed, sigma)
+    kind = flags & 7
+    gam[(kind == VEL) | (kind == PRES)] = 1.0
+    gam[kind == WALL] = 0.0
+    width = min(wy, wz)
+    tau = tau_from_re(re, umax, width)
+    nu = (tau - 0.5) / 3.0
+    lat = Lattice(f"heat_sink_{nx}x{ny}x{nz}", D3Q19, nx, ny, nz, flags.ravel(),
+                  gam.ravel(), bc.ravel(), tau=tau, gamma_model=gamma_model,
+                  thermal=True, kappa_f=nu / pr, k_ratio=k_ratio, q_flux=q_flux,
+                  T0=0.0, w_pin=w_pin, w_tmean=w_tmean)
+    lat.meta.update(width=width, umax=umax, re=re, pr=pr, seed=seed)
+    return lat
+
+
+def random_fields(lat: Lattice, seed: int, scale: float = 1.0):
+    """Seeded N(0,1) vectors shaped like a population field (for dot tests)."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal(lat.n)
+
+
+def config_lattices(which: int, **kw):
+    """The synthetic stand-ins for the five benchmark configurations."""
+    if which == 1:
+        return pipe_bend_2d(**kw)
+    if which == 2:
+        return pipe_bend_3d(**kw)
+    if which == 3:
+        return heat_sink(**kw)
+    if which == 4:
+        kw.setdefault("nx", 96)
+        kw.setdefault("ny", 48)
+        kw.setdefault("nz", 24)
+        return heat_sink(**kw)
+    raise ValueError(which)
