@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Forward + adjoint MLUPS of the discrete adjoint LBM on one GB300 per rank.
+
+One step = for each Re of the workload: forward solve to the residual
+tolerance, adjoint solve to the residual tolerance and dJ/dgamma, from rest,
+with inputs already resident in HBM.  value = cell updates (forward + adjoint
+steps x nodes, summed over ranks) / max-over-ranks time.  L2 is flushed
+between timed steps by writing a buffer larger than L2.
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload on the host cores (there is no reference code to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint MLUPS (% HBM roofline); served sens/s & p50/p99 vs plain FP32"
+RES = (50.0, 100.0, 500.0)
+TOL = 1e-6
+CAP = 200000
+CHECK = 1000
+FWD_BYTES = {"fp32": 19 * 4 * 2 + 4 + 1, "fp64": 19 * 8 * 2 + 8 + 1,
+             "fp16": 19 * 2 * 2 + 4 + 1, "bf16": 19 * 2 * 2 + 4 + 1}
+ADJ_BYTES = {"fp32": 19 * 4 * 2 + 12 + 4 + 1, "fp64": 19 * 8 * 2 + 24 + 8 + 1,
+             "fp16": 19 * 4 * 2 + 12 + 4 + 1, "bf16": 19 * 4 * 2 + 12 + 4 + 1}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=64, help="pipe-bend lattice edge")
+    p.add_argument("--storage", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
+    p.add_argument("--roof-n", type=int, default=320, help="edge of the >L2 roofline lattice")
+    p.add_argument("--roof-launches", type=int, default=20)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mode", default="full", choices=["full", "kernels"],
+                   help="kernels: only time the fused step kernels on a --roof-n lattice")
+    return p.parse_args()
+
+
+def run_kernels(args):
+    """Per-launch time and achieved GB/s of the fused forward and adjoint
+    kernels on a pipe bend of edge --roof-n (CUDA events on their stream)."""
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    hbm, kind = peaks()
+    big = I.pipe_bend_3d(n=args.roof_n, re=100.0, seed=1)
+    sb = Solver.from_lattice(big, storage=args.storage, device="cuda:0")
+    sb.forward(tol=0, max_steps=2, check_every=2, reset=True)
+    sb.time_steps(0, 3)
+    fwd_ms = sb.time_steps(0, args.roof_launches)
+    sb.time_steps(2, 3)
+    adj_ms = sb.time_steps(2, args.roof_launches)
+    nb = big.n
+    out = {"mode": "kernels", "lattice": [args.roof_n] * 3, "storage": args.storage,
+           "nodes": nb, "peak_GB/s": hbm, "peak_kind": kind}
+    for name, ms, bpn in (("forward", fwd_ms, FWD_BYTES[args.storage]),
+                          ("adjoint", adj_ms, ADJ_BYTES[args.storage])):
+        gbs = bpn * nb / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_launch": ms, "bytes_per_node": bpn, "GB/s": round(gbs, 1),
+                     "frac": round(gbs / hbm, 4), "MLUPS": round(nb / (ms * 1e-3) / 1e6, 1)}
+    print(json.dumps(out))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300 import _capi as C
+    from paper_2501_02161_gb300.solver import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    C.lib()
+
+    lats = {re: I.pipe_bend_3d(n=args.n, re=re, seed=1) for re in RES}
+    N = lats[RES[0]].n
+    solvers = {re: Solver.from_lattice(lat, storage=args.storage, device=dev)
+               for re, lat in lats.items()}
+    sens = torch.empty(N, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        ups, launches, per = 0, 0, {}
+        for re, s in solvers.items():
+            rf = s.forward(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
+            ra = (s.adjoint(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
+                  if rf.status >= 0 else rf.__class__(0, float("nan"), 0.0, 0.0, 0.0, rf.status))
+            if ra.status >= 0:
+                s.sensitivity(out=sens)
+            ups += (rf.steps + ra.steps) * N
+            launches += (rf.steps + math.ceil(rf.steps / CHECK) + 1 +
+                         ra.steps + math.ceil(ra.steps / CHECK) + 1 + 1)
+            per[re] = {"fwd_steps": rf.steps, "adj_steps": ra.steps, "J": rf.J,
+                       "fwd_residual": rf.residual, "adj_residual": ra.residual,
+                       "status": [C.STATUS_NAMES[rf.status], C.STATUS_NAMES[ra.status]]}
+        return ups, launches, per
+
+    for _ in range(args.warmup):
+        one_step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, total_ups, total_launch, per = 0.0, 0, 0, None
+    for _ in range(args.steps):
+        flush.fill_(float(_))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ups, nl, per = one_step()
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_ups += ups
+        total_launch += nl
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(total_ups)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ups = float(u.item())
+    value = total_ups / (total_ms * 1e-3) / 1e6
+
+    hbm, peak_kind = peaks()
+    # kernel time shares inside the workload: per-launch duration at 64^3
+    s0 = solvers[RES[1]]
+    s0.forward(tol=0, max_steps=2, check_every=2, reset=True)
+    fwd_ms_w = s0.time_steps(0, 200)
+    adj_ms_w = s0.time_steps(2, 200)
+    fsteps = sum(v["fwd_steps"] for v in per.values())
+    asteps = sum(v["adj_steps"] for v in per.values())
+    fwd_share = fsteps * fwd_ms_w / (fsteps * fwd_ms_w + asteps * adj_ms_w)
+    at_workload = {
+        "fwd": {"ms": fwd_ms_w, "GB/s": FWD_BYTES[args.storage] * N / (fwd_ms_w * 1e-3) / 1e9},
+        "adj": {"ms": adj_ms_w, "GB/s": ADJ_BYTES[args.storage] * N / (adj_ms_w * 1e-3) / 1e9},
+        "fwd_time_share": fwd_share,
+        "note": f"{args.n}^3 populations fit in L2 (129 MB); rates above HBM are L2 rates"}
+
+    roof = None
+    if args.roof_n > 0:
+        del solvers
+        torch.cuda.empty_cache()
+        big = I.pipe_bend_3d(n=args.roof_n, re=100.0, seed=1)
+        sb = Solver.from_lattice(big, storage=args.storage, device=dev)
+        sb.forward(tol=0, max_steps=2, check_every=2, reset=True)
+        sb.time_steps(0, 3)
+        fwd_ms = sb.time_steps(0, args.roof_launches)
+        sb.time_steps(2, 3)
+        adj_ms = sb.time_steps(2, args.roof_launches)
+        nb = big.n
+        kern = "adjoint" if fwd_share < 0.5 else "forward"
+        ms = adj_ms if kern == "adjoint" else fwd_ms
+        byts = (ADJ_BYTES if kern == "adjoint" else FWD_BYTES)[args.storage] * nb
+        ach = byts / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                "kernel": f"k_flow_{'adjoint' if kern == 'adjoint' else 'step'} D3Q19 {args.storage}",
+                "workload": f"pipe bend {args.roof_n}^3 ({nb} nodes, {byts/1e9:.2f} GB algorithmic per launch)",
+                "bytes_per_node": (ADJ_BYTES if kern == "adjoint" else FWD_BYTES)[args.storage],
+                "ms_per_launch": ms,
+                "other": {"forward_GB/s": round(FWD_BYTES[args.storage] * nb / (fwd_ms * 1e-3) / 1e9, 1),
+                          "adjoint_GB/s": round(ADJ_BYTES[args.storage] * nb / (adj_ms * 1e-3) / 1e9, 1),
+                          "forward_MLUPS": round(nb / (fwd_ms * 1e-3) / 1e6, 1),
+                          "adjoint_MLUPS": round(nb / (adj_ms * 1e-3) / 1e6, 1)}}
+        sb.close()
+        del sb
+        torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, lats, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(lats[RES[1]], fwd_steps=20, adj_steps=6)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64",
+                                                               "fp16": "f16-offset/f32",
+                                                               "bf16": "bf16-offset/f32"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": f"3D D3Q19 pipe bend {args.n}^3, gamma = filtered noise (seed 1), "
+                                   f"Re in {list(RES)}, forward + adjoint to residual {TOL} + dJ/dgamma",
+                       "lattice": [args.n] * 3, "storage": args.storage, "check_every": CHECK,
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "per_re": {str(k): v for k, v in per.items()},
+            "roofline": roof, "roofline_at_workload": at_workload,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(total_launch),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, lats, dev):
+    """Same metric through the C-ABI with host buffers: each step uploads the
+    inputs (flags, gamma, boundary values) from pinned host memory and reads
+    dJ/dgamma back; the copies are inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_2501_02161_gb300.solver import Solver
+
+    host = {}
+    for re, lat in lats.items():
+        host[re] = (torch.from_numpy(lat.flags.copy()).pin_memory(),
+                    torch.from_numpy(lat.gamma.astype(np.float32)).pin_memory(),
+                    torch.from_numpy(lat.bcval.astype(np.float32)).pin_memory())
+    N = lats[RES[0]].n
+    out = torch.empty(N, dtype=torch.float32).pin_memory()
+    solvers = {re: Solver.from_lattice(lat, storage=args.storage, device=dev)
+               for re, lat in lats.items()}
+
+    def step():
+        ups = 0
+        for re, s in solvers.items():
+            fl, ga, bc = host[re]
+            s.set_flags(fl)
+            s.set_gamma(ga)
+            s.set_bc_values(bc)
+            rf = s.forward(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
+            if rf.status < 0:
+                ups += rf.steps * N
+                continue
+            ra = s.adjoint(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
+            if ra.status >= 0:
+                s.sensitivity(out=out)
+            ups += (rf.steps + ra.steps) * N
+        return ups
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ups = 0
+    for _ in range(max(1, args.steps)):
+        ups += step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for s in solvers.values():
+        s.close()
+    return {"value": round(ups / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(len(RES) * N * (1 + 4 + 16)),
+            "d2h_bytes_per_step": int(len(RES) * N * 4)}
+
+
+def cpu_baseline(lat, fwd_steps, adj_steps):
+    """The FP64 oracle on a bounded sample of the same workload (host cores)."""
+    from oracle import oracle as O
+    O.build()
+    orc = O.Oracle(lat)
+    t0 = time.perf_counter()
+    orc.flow_run(fwd_steps)
+    t1 = time.perf_counter()
+    orc.adjoint_run(adj_steps)
+    t2 = time.perf_counter()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    ups = (fwd_steps + adj_steps) * lat.n
+    return {"value": round(ups / (t2 - t0) / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{lat.name} Re={lat.meta.get('re')}: {fwd_steps} forward + {adj_steps} "
+                      f"adjoint steps from rest, FP64, OpenMP over nodes "
+                      f"(forward {fwd_steps * lat.n / (t1 - t0) / 1e6:.2f} MLUPS, "
+                      f"adjoint {adj_steps * lat.n / (t2 - t1) / 1e6:.2f} MLUPS)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2501_02161_gb300 import inputs as I
+    lats = {re: I.pipe_bend_3d(n=args.n, re=re, seed=1) for re in RES}
+    fwd, adj = 8, 2
+
+    def step():
+        t0 = time.perf_counter()
+        ups = 0
+        from oracle import oracle as O
+        for lat in lats.values():
+            orc = O.Oracle(lat)
+            orc.flow_run(fwd)
+            orc.adjoint_run(adj)
+            ups += (fwd + adj) * lat.n
+        return ups, time.perf_counter() - t0
+
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        step()
+    tot_u, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        u, t = step()
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_t / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3D D3Q19 pipe bend {args.n}^3, Re in {list(RES)}; "
+                                   f"bounded sample per step: {fwd} forward + {adj} adjoint steps per Re",
+                       "lattice": [args.n] * 3},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{fwd} forward + {adj} adjoint oracle steps per Re from rest"},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.mode == "kernels":
+        run_kernels(a)
+    else:
+        run_ours(a)

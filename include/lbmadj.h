@@ -1,0 +1,198 @@
+/*
+ * lbmadj.h -- C-ABI of the GB300 (sm_103a) discrete adjoint lattice Boltzmann
+ * solver.
+ *
+ * The calls follow the problem statement of the paper (arXiv 2501.02161):
+ *   lattice + stencil            Sec. 2.1, Eq. 2-5 (D2Q9, D3Q19)
+ *   node flags                   Sec. 2.1, Eq. 7-9 (fluid, wall, inlet, outlet)
+ *   design field gamma           Sec. 2.2, Eq. 11-12 (relaxed to [0, 1])
+ *   relaxation time tau          Eq. 3 (nu = (tau - 1/2)/3)
+ *   objective                    Eq. 34 (inlet pressure, steady form) and a
+ *                                mean-temperature term for heat sinks (Sec. 3.3)
+ *   forward, adjoint, dJ/dgamma  Eq. 35-37, 53-56 / 59-61 / 64-65, 66
+ *   temperature lattice          Eq. 71 (D3Q7, coupled through the frozen flow)
+ *
+ * Conventions shared by every call
+ *   - Every function returns an lbm_status (0 = success, > 0 = warning with
+ *     usable results, < 0 = error).  lbm_last_error() gives a message.
+ *   - Lattice nodes are numbered n = x + nx*(y + ny*z), x fastest.
+ *   - Inputs are copied into buffers the context owns; the caller keeps
+ *     ownership of what it passes.  Outputs go to caller-owned buffers.
+ *   - A pointer argument with on_device != 0 is a CUDA device pointer on the
+ *     context's device (for example torch.Tensor.data_ptr()); with
+ *     on_device == 0 it is ordinary host memory.
+ *   - dtype codes: LBM_DTYPE_F64 (double) or LBM_DTYPE_F32 (float).
+ *   - Work is ordered after all work already queued on the stream given to
+ *     lbm_set_stream (default: the legacy default stream), and that stream
+ *     waits for the call's work before the call returns control to it.  Calls
+ *     that report numbers (solves, lbm_get_*) synchronise.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Node flag byte (bit-exact, identical in every call):
+ *   bits 0-2  type: 0 FLUID, 1 WALL (full-way bounce-back, no collision,
+ *             Eq. 9), 2 VEL (Zou-He velocity, Eq. 7), 3 PRES (Zou-He fixed
+ *             density, Eq. 8)
+ *   bits 3-5  inward normal of an open boundary or heated wall:
+ *             0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
+ *   bit 6     HEAT: a WALL node that adds q_flux per step to the temperature
+ *             population along its normal
+ *   bit 7     must be 0
+ *
+ * Boundary values, 4 numbers per node, read only at VEL / PRES nodes:
+ *   VEL: (ux, uy, uz, T_in)       PRES: (rho_out, unused, unused, unused)
+ *
+ * Population order (for lbm_get_adjoint / state export):
+ *   D2Q9  : 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+,+), 6 (-,+), 7 (-,-), 8 (+,-)
+ *           (the order Eq. 7-8 use)
+ *   D3Q19 : 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z, 7 (1,1,0), 8 (-1,-1,0),
+ *           9 (1,-1,0), 10 (-1,1,0), 11 (1,0,1), 12 (-1,0,-1), 13 (1,0,-1),
+ *           14 (-1,0,1), 15 (0,1,1), 16 (0,-1,-1), 17 (0,1,-1), 18 (0,-1,1)
+ *   D3Q7  : 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z
+ */
+#ifndef LBMADJ_H
+#define LBMADJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_NOT_CONVERGED = 1,   /* step cap reached above tolerance; results kept */
+    LBM_ERR_ARG = -1,        /* bad argument (null, size, code, range) */
+    LBM_ERR_OOM = -2,        /* device allocation failed / budget exceeded */
+    LBM_ERR_CUDA = -3,       /* a CUDA call failed; see lbm_last_error */
+    LBM_ERR_DIVERGED = -4,   /* non-finite residual or objective */
+    LBM_ERR_ORDER = -5,      /* call made before the step it depends on */
+    LBM_ERR_UNSUPPORTED = -6 /* combination not built (e.g. D2Q9 + thermal) */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_stencil;
+
+/* Population storage.  FP16/BF16 store f - w_i * rho0 (flow) and
+ * g - w_k * T0 (temperature) and compute in FP32. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_OFS = 2, LBM_BF16_OFS = 3 } lbm_storage;
+
+typedef enum { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 } lbm_dtype;
+
+/* How gamma enters the equilibrium.  EQ12: u <- gamma u inside Eq. 4, as
+ * Eq. 12 writes it.  LINEAR: f^eq = w (rho + gamma rho0 [...](u)), the model
+ * whose gamma-derivative is the bracket printed in Eq. 66.  Both agree for
+ * binary designs (Eq. 11) and both give the momentum drag (1-gamma)/tau. */
+typedef enum { LBM_GAMMA_EQ12 = 0, LBM_GAMMA_LINEAR = 1 } lbm_gamma_model;
+
+typedef struct {
+    double tau;        /* flow relaxation time, > 0.5 (Eq. 2-3) */
+    double rho0;       /* constant density of the incompressible model (Eq. 4) */
+    int gamma_model;   /* lbm_gamma_model */
+    double kappa_f;    /* fluid thermal diffusivity; tau_g = 1/2 + 4 kappa(gamma) */
+    double k_ratio;    /* solid/fluid conductivity ratio: kappa = kappa_f (gamma + (1-gamma) k_ratio) */
+    double q_flux;     /* heat per step added at HEAT wall nodes */
+    double T0;         /* initial temperature (and 16-bit storage offset) */
+} lbm_params;
+
+typedef struct {
+    double w_pin;      /* weight of J_p = (1/(3 N_in)) sum_{VEL nodes} rho  (Eq. 34, steady) */
+    double w_tmean;    /* weight of J_T = (1/N_nonwall) sum_{non-wall nodes} T */
+} lbm_objective;
+
+typedef struct {
+    double tol;          /* stop when |I(t)-I(t-K)|/|I(t)| < tol; tol <= 0: run exactly max_steps */
+    long long max_steps; /* step cap (or exact count when tol <= 0); >= 0 */
+    int check_every;     /* K, steps between residual checks (> 0; the paper uses 1000) */
+    int reset;           /* 1: restart from the initial state; 0: continue (warm start) */
+} lbm_solve_opts;
+
+typedef struct {
+    long long steps;     /* steps taken in this call */
+    double residual;     /* last |I(t)-I(t-K)|/|I(t)| */
+    double I;            /* last residual quantity (mean |u|, mean T, mean sum |f*|) */
+    double J;            /* objective at the last check (forward calls) */
+    double ms;           /* wall time of the call in milliseconds */
+    int status;          /* lbm_status of the phase */
+} lbm_report;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a context for an nx*ny*nz lattice (nz = 1 for D2Q9).  Allocates all
+ * device state (populations double-buffered, adjoint, frozen fields).
+ * thermal != 0 adds the D3Q7 temperature lattice (D3Q19 only).
+ * Errors: LBM_ERR_ARG (sizes <= 0, nz != 1 for D2Q9, unknown codes),
+ * LBM_ERR_UNSUPPORTED (thermal with D2Q9), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(lbm_ctx** out, int stencil, int nx, int ny, int nz, int storage,
+                      int thermal);
+/* Free every device buffer the context owns.  Null is accepted. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Order the context's work after the given cudaStream_t (e.g.
+ * torch.cuda.current_stream().cuda_stream; 0 = legacy default stream). */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Node flags, n = nx*ny*nz bytes, layout above.  Rejects bit 7, unknown
+ * types, and open boundaries whose normal is not along an axis of the lattice
+ * (LBM_ERR_ARG).  Invalidates forward and adjoint results. */
+lbm_status lbm_set_flags(lbm_ctx* ctx, const uint8_t* flags, size_t n, int on_device);
+/* Design field gamma in [0, 1], n values of dtype (Eq. 11-12). */
+lbm_status lbm_set_gamma(lbm_ctx* ctx, const void* gamma, size_t n, int dtype, int on_device);
+/* Boundary values, n = 4*nx*ny*nz values of dtype, layout above. */
+lbm_status lbm_set_bc_values(lbm_ctx* ctx, const void* values, size_t n, int dtype,
+                             int on_device);
+/* Physical parameters.  tau <= 0.5, rho0 <= 0, kappa_f < 0 with thermal on,
+ * k_ratio <= 0 or an unknown gamma model give LBM_ERR_ARG. */
+lbm_status lbm_set_params(lbm_ctx* ctx, const lbm_params* p);
+lbm_status lbm_set_objective(lbm_ctx* ctx, const lbm_objective* obj);
+
+/* Forward solve (Eq. 35): the flow to its residual tolerance, then, with the
+ * thermal lattice on, the temperature with the converged velocity frozen.
+ * Stores the frozen u (and T) the adjoint needs.  Returns LBM_NOT_CONVERGED
+ * when a phase hits max_steps above tol, LBM_ERR_DIVERGED on non-finite
+ * values.  rep may be null; rep->steps counts flow + thermal steps. */
+lbm_status lbm_forward(lbm_ctx* ctx, const lbm_solve_opts* opts, lbm_report* rep);
+
+/* Adjoint solve (Eq. 53-56 iterated to a fixed point from f*_C = 0): the
+ * temperature adjoint first (thermal on), then the flow adjoint with the
+ * thermal coupling term.  Needs a completed lbm_forward (else LBM_ERR_ORDER). */
+lbm_status lbm_adjoint(lbm_ctx* ctx, const lbm_solve_opts* opts, lbm_report* rep);
+
+/* dJ/dgamma per node (Eq. 66 without the volume multiplier lambda, plus the
+ * temperature terms when thermal is on), n = nx*ny*nz values of dtype into
+ * caller memory.  Zero at WALL nodes.  Needs lbm_adjoint (LBM_ERR_ORDER). */
+lbm_status lbm_sensitivity(lbm_ctx* ctx, void* out, int dtype, int on_device);
+
+/* Macroscopic fields of the converged forward state, each n (rho, T) or 3n
+ * (u, component-major: u[a*n + node]) values of dtype; any may be null.
+ * T needs thermal on.  Needs lbm_forward (LBM_ERR_ORDER). */
+lbm_status lbm_get_fields(lbm_ctx* ctx, void* rho, void* u, void* T, int dtype,
+                          int on_device);
+
+/* Objective J of the converged forward state (host double). */
+lbm_status lbm_get_objective(lbm_ctx* ctx, double* J);
+
+/* Adjoint populations after the adjoint boundary step (f* = B^T f*_C, the
+ * stored iterate), Q*n values, population-major: fstar[i*n + node]; gstar:
+ * 7*n values.  Either may be null. */
+lbm_status lbm_get_adjoint(lbm_ctx* ctx, void* fstar, void* gstar, int dtype, int on_device);
+
+/* Time n plain fused steps of one phase on the context's stream with CUDA
+ * events recorded on that stream (after all queued work) and write the mean
+ * milliseconds per launch.  phase: 0 flow forward, 1 temperature forward,
+ * 2 flow adjoint, 3 temperature adjoint.  The steps advance that phase's state
+ * exactly as a solve would; no reduction runs.  Needs the inputs set
+ * (LBM_ERR_ORDER) and, for phases 1-3, a completed lbm_forward. */
+lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
+
+/* Message for the last error on this thread (static storage, valid until the
+ * next call on this thread). */
+const char* lbm_last_error(void);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMADJ_H */

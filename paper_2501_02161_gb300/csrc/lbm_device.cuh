@@ -1,0 +1,852 @@
+// lbm_device.cuh -- device-side lattice tables, population storage policies and
+// the fused kernels of the forward / adjoint lattice Boltzmann sweeps.
+//
+// Memory layout (structure of arrays): population i of node n lives at
+// p[i*np + n], n = x + nx*(y + ny*z), np = node count rounded up to a multiple
+// of 64 so every population plane starts 256-byte aligned.  One thread owns one
+// node; a block is a (BX x BY) tile of an x-y plane so that a warp reads 32
+// consecutive x of one plane of one population (coalesced, with the +/-1 shift
+// of the pull straddling at most one extra 32-byte sector).
+//
+// The flow kernels work on offset populations h_i = f_i - w_i rho0 in every
+// storage type (rho - rho0 = sum h, rho0 u = sum e h), so no FP32 digits are
+// spent on the constant w_i rho0; 16-bit storage holds the same h.
+//
+// Forward step (Eq. 35-37): pull f_S,i(x) = f_C,i(x - e_i) with periodic wrap,
+// boundary operator B at the node, BGK collision with the design coupling
+// u <- gamma u (Eq. 12) and store f_C.  Adjoint step (Eq. 53-56): pull
+// f*_S,i(x) = f*_i(x + e_i) (Eq. 61), C^T in moment form (Eq. 65), objective
+// source, closed-form B^T (Eq. 59-60 generalised), store f*.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum : int { FLUID = 0, WALL = 1, VEL = 2, PRES = 3 };
+constexpr int HEAT_BIT = 0x40;
+
+// ---------------------------------------------------------------------------
+// lattices (Eq. 5); D2Q9 in the order Eq. 7-8 use
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19;
+    static constexpr int D = 3;
+    // rest; +/-x, +/-y, +/-z; (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+    // (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+             : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+             : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+             : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+// temperature lattice: rest 1/4, six axis directions 1/8 (c_s^2 = 1/4)
+struct D3Q7 {
+    static constexpr int Q = 7;
+    __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+    __host__ __device__ static constexpr int cy(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+    __host__ __device__ static constexpr int cz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 0.25 : 0.125; }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// population storage: full precision, or 16-bit offsets from a reference
+// ---------------------------------------------------------------------------
+template <typename T> struct Pop;
+template <> struct Pop<double> {
+    using R = double;
+    __device__ __forceinline__ static R ld(const double* __restrict__ p, size_t k, R) { return __ldg(p + k); }
+    __device__ __forceinline__ static void st(double* __restrict__ p, size_t k, R v, R) { p[k] = v; }
+    __device__ __forceinline__ static double enc(R v, R) { return v; }
+};
+template <> struct Pop<float> {
+    using R = float;
+    __device__ __forceinline__ static R ld(const float* __restrict__ p, size_t k, R) { return __ldg(p + k); }
+    __device__ __forceinline__ static void st(float* __restrict__ p, size_t k, R v, R) { p[k] = v; }
+    __device__ __forceinline__ static float enc(R v, R) { return v; }
+};
+template <> struct Pop<__half> {
+    using R = float;
+    __device__ __forceinline__ static R ld(const __half* __restrict__ p, size_t k, R off) {
+        return off + __half2float(__ldg(p + k));
+    }
+    __device__ __forceinline__ static void st(__half* __restrict__ p, size_t k, R v, R off) {
+        p[k] = __float2half_rn(v - off);
+    }
+    __device__ __forceinline__ static __half enc(R v, R off) { return __float2half_rn(v - off); }
+};
+template <> struct Pop<__nv_bfloat16> {
+    using R = float;
+    __device__ __forceinline__ static R ld(const __nv_bfloat16* __restrict__ p, size_t k, R off) {
+        return off + __bfloat162float(__ldg(p + k));
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16* __restrict__ p, size_t k, R v, R off) {
+        p[k] = __float2bfloat16_rn(v - off);
+    }
+    __device__ __forceinline__ static __nv_bfloat16 enc(R v, R off) { return __float2bfloat16_rn(v - off); }
+};
+
+// ---------------------------------------------------------------------------
+// kernel arguments (passed by value)
+// ---------------------------------------------------------------------------
+template <typename T, typename TA, typename R>
+struct FlowArgs {
+    const T* __restrict__ fin;       // forward populations (read)
+    T* __restrict__ fout;            // forward populations (write)
+    const TA* __restrict__ ain;      // adjoint populations (read)
+    TA* __restrict__ aout;           // adjoint populations (write)
+    const uint8_t* __restrict__ flags;
+    const R* __restrict__ gamma;
+    const R* __restrict__ bc;        // 4 values per node
+    const R* __restrict__ u;         // frozen velocity, 3 planes of np
+    const R* __restrict__ cpl;       // thermal coupling v / rho0, 3 planes (or null)
+    const R* __restrict__ sT;        // thermal part of dJ/dgamma (or null)
+    R* __restrict__ out0;            // rho (reducing step, init) / dJ/dgamma (sens)
+    R* __restrict__ out1;            // u, 3 planes (reducing step, init)
+    double* __restrict__ partials;   // per-block sums (reductions)
+    int nx, ny, nz;
+    long long np;
+    R omega;                         // 1/tau
+    R rho0;
+    R src_in;                        // w_pin / (3 N_in): -dJ/df_i at VEL nodes
+    R ascale;                        // adjoint storage scale (16-bit adjoint), 1 otherwise
+    int model;                       // 0 EQ12, 1 LINEAR
+};
+
+template <typename T, typename TA, typename R>
+struct ThermArgs {
+    const T* __restrict__ gin;
+    T* __restrict__ gout;
+    const TA* __restrict__ ain;
+    TA* __restrict__ aout;
+    const uint8_t* __restrict__ flags;
+    const R* __restrict__ gamma;
+    const R* __restrict__ bc;
+    const R* __restrict__ u;         // frozen flow velocity, 3 planes
+    const R* __restrict__ gpost;     // frozen post-boundary g, 7 planes
+    R* __restrict__ gcn;             // adjoint g*_C of the outlet's unknown (PRES nodes)
+    R* __restrict__ out0;            // T (reducing step, init) / v (coupling, 3 planes)
+    R* __restrict__ out1;            // post-boundary g (reducing step, init, 7 planes) / sT (coupling)
+    double* __restrict__ partials;
+    int nx, ny, nz;
+    long long np;
+    R rho0, kappa_f, k_ratio, q, T0;
+    R src_T;                         // w_tmean / N_nonwall
+    R ascale;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+struct Cell {
+    int x, y, z;
+    long long n;
+    bool active;
+};
+
+__device__ __forceinline__ Cell this_cell(int nx, int ny) {
+    Cell c;
+    c.x = blockIdx.x * blockDim.x + threadIdx.x;
+    c.y = blockIdx.y * blockDim.y + threadIdx.y;
+    c.z = blockIdx.z;
+    c.active = (c.x < nx) && (c.y < ny);
+    c.n = c.x + (long long)nx * (c.y + (long long)ny * c.z);
+    return c;
+}
+
+// node index of x + s*e_i with periodic wrap (s = +1 or -1)
+template <class L>
+__device__ __forceinline__ long long shifted(const Cell& c, int i, int s, int nx, int ny, int nz) {
+    int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
+    int x = c.x + dx, y = c.y + dy, z = c.z + dz;
+    x = x < 0 ? nx - 1 : (x >= nx ? 0 : x);
+    y = y < 0 ? ny - 1 : (y >= ny ? 0 : y);
+    z = z < 0 ? nz - 1 : (z >= nz ? 0 : z);
+    return x + (long long)nx * (y + (long long)ny * z);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* __restrict__ partials) {
+    __shared__ double sh[NV][32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nwarps ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) partials[b * NV + k] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward boundary operator: Zou-He with an axis-aligned inward normal
+//   unknowns U = {i : e_i.n > 0};  K0 = sum_{e.n=0} f, K- = sum_{e.n<0} f
+//   VEL: u given.  PRES: u = n (rho_out - K0 - 2K-)/rho0 (Eq. 8, first line)
+//   f_i = f_opp(i) + 6 w_i rho0 e_i.u - e_i.N,  N = S/2 - rho0 u_t / 3
+//   with S = sum_{e.n=0} e f (Eq. 7-8 written for any face); applied to the
+//   offset populations h (w_i = w_opp(i), sum_{e.n=0} e w = 0)
+// ---------------------------------------------------------------------------
+template <class L, typename R>
+__device__ __forceinline__ void zou_he(R (&f)[L::Q], int type, int code, const R* __restrict__ bc, R rho0) {
+    const int ax = code >> 1;
+    const int sg = (code & 1) ? -1 : 1;
+    const int n0 = ax == 0 ? sg : 0, n1 = ax == 1 ? sg : 0, n2 = ax == 2 ? sg : 0;
+    R K0 = 0, Km = 0, S0 = 0, S1 = 0, S2 = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
+        if (d == 0) {
+            K0 += f[i];
+            S0 += R(L::cx(i)) * f[i];
+            S1 += R(L::cy(i)) * f[i];
+            S2 += R(L::cz(i)) * f[i];
+        } else if (d < 0) {
+            Km += f[i];
+        }
+    }
+    R u0, u1, u2;
+    if (type == VEL) {
+        u0 = bc[0];
+        u1 = bc[1];
+        u2 = bc[2];
+    } else {
+        // sums of offset populations: sum_{e.n=0} w + 2 sum_{e.n<0} w = 1
+        const R un = (bc[0] - rho0 - K0 - R(2) * Km) / rho0;
+        u0 = un * R(n0);
+        u1 = un * R(n1);
+        u2 = un * R(n2);
+    }
+    const R unn = u0 * R(n0) + u1 * R(n1) + u2 * R(n2);
+    const R t0 = u0 - unn * R(n0), t1 = u1 - unn * R(n1), t2 = u2 - unn * R(n2);
+    const R third = R(1) / R(3);
+    const R N0 = R(0.5) * S0 - rho0 * third * t0;
+    const R N1 = R(0.5) * S1 - rho0 * third * t1;
+    const R N2 = R(0.5) * S2 - rho0 * third * t2;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
+        if (d > 0) {
+            const R eu = R(L::cx(i)) * u0 + R(L::cy(i)) * u1 + R(L::cz(i)) * u2;
+            const R eN = R(L::cx(i)) * N0 + R(L::cy(i)) * N1 + R(L::cz(i)) * N2;
+            f[i] = f[L::opp(i)] + R(6.0 * L::w(i)) * rho0 * eu - eN;
+        }
+    }
+}
+
+// adjoint boundary operator f* = B^T f*_C for a Zou-He node:
+//   unknown j           : 0
+//   e_j.n < 0           : c_j + c_opp(j)              (- 2P at PRES)
+//   e_j.n = 0           : c_j - e_j.M / 2              (-  P at PRES)
+// with M = sum_{k in U} e_k c_k and P = sum_{k in U} 6 w_k c_k.  In D2Q9 this is
+// Eq. 59 (left velocity inlet) and Eq. 60 (bottom fixed-density outlet).
+template <class L, typename R>
+__device__ __forceinline__ void zou_he_adjoint(R (&c)[L::Q], int type, int code) {
+    const int ax = code >> 1;
+    const int sg = (code & 1) ? -1 : 1;
+    const int n0 = ax == 0 ? sg : 0, n1 = ax == 1 ? sg : 0, n2 = ax == 2 ? sg : 0;
+    R M0 = 0, M1 = 0, M2 = 0, P = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
+        if (d > 0) {
+            M0 += R(L::cx(i)) * c[i];
+            M1 += R(L::cy(i)) * c[i];
+            M2 += R(L::cz(i)) * c[i];
+            P += R(6.0 * L::w(i)) * c[i];
+        }
+    }
+    if (type != PRES) P = R(0);
+    R out[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
+        if (d > 0)
+            out[i] = R(0);
+        else if (d < 0)
+            out[i] = c[i] + c[L::opp(i)] - R(2) * P;
+        else
+            out[i] = c[i] - R(0.5) * (R(L::cx(i)) * M0 + R(L::cy(i)) * M1 + R(L::cz(i)) * M2) - P;
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) c[i] = out[i];
+}
+
+template <class L, typename R>
+__device__ __forceinline__ void bounce(R (&f)[L::Q]) {
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        if (L::opp(i) > i) {
+            const R t = f[i];
+            f[i] = f[L::opp(i)];
+            f[L::opp(i)] = t;
+        }
+    }
+}
+
+// pull the post-collision populations of the upstream neighbours and apply B
+template <class L, typename T, typename TA, typename R>
+__device__ __forceinline__ int pull_forward(const FlowArgs<T, TA, R>& a, const Cell& c, R (&f)[L::Q]) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const long long src = shifted<L>(c, i, -1, a.nx, a.ny, a.nz);
+        f[i] = Pop<T>::ld(a.fin, (size_t)i * a.np + src, R(0));
+    }
+    const int fl = a.flags[c.n];
+    const int type = fl & 7;
+    if (type == WALL)
+        bounce<L>(f);
+    else if (type >= VEL)
+        zou_he<L>(f, type, (fl >> 3) & 7, a.bc + 4 * c.n, a.rho0);
+    return fl;
+}
+
+// drho = rho - rho0 = sum h, u = sum e h / rho0
+template <class L, typename R>
+__device__ __forceinline__ void moments(const R (&f)[L::Q], R rho0, R& rho, R& u0, R& u1, R& u2) {
+    R r = 0, j0 = 0, j1 = 0, j2 = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        r += f[i];
+        if (L::cx(i)) j0 += R(L::cx(i)) * f[i];
+        if (L::cy(i)) j1 += R(L::cy(i)) * f[i];
+        if (L::cz(i)) j2 += R(L::cz(i)) * f[i];
+    }
+    const R inv = R(1) / rho0;
+    rho = r;
+    u0 = j0 * inv;
+    u1 = j1 * inv;
+    u2 = j2 * inv;
+}
+
+// ---------------------------------------------------------------------------
+// forward kernels
+// ---------------------------------------------------------------------------
+template <class L, typename T, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_flow_step(FlowArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    double acc[2] = {0.0, 0.0};
+    if (c.active) {
+        R f[L::Q];
+        const int fl = pull_forward<L>(a, c, f);
+        const int type = fl & 7;
+        R drho, u0, u1, u2;
+        moments<L>(f, a.rho0, drho, u0, u1, u2);
+        if (REDUCE) {  // the fields and the frozen velocity of this post-boundary state
+            a.out0[c.n] = a.rho0 + drho;
+            a.out1[c.n] = u0;
+            a.out1[a.np + c.n] = u1;
+            a.out1[2 * a.np + c.n] = u2;
+        }
+        if (type != WALL) {
+            if (REDUCE) {
+                acc[0] = sqrt((double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2);
+                if (type == VEL) acc[1] = (double)a.rho0 + (double)drho;
+            }
+            const R g = a.gamma[c.n];
+            R a0, a1, a2, amp;
+            if (a.model == 0) {
+                a0 = g * u0; a1 = g * u1; a2 = g * u2; amp = R(1);
+            } else {
+                a0 = u0; a1 = u1; a2 = u2; amp = g;
+            }
+            const R uu = a0 * a0 + a1 * a1 + a2 * a2;
+            const R om = a.omega;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const R eu = R(L::cx(i)) * a0 + R(L::cy(i)) * a1 + R(L::cz(i)) * a2;
+                const R heq = R(L::w(i)) * (drho + a.rho0 * amp * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
+                f[i] += om * (heq - f[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            Pop<T>::st(a.fout, (size_t)i * a.np + c.n, f[i], R(0));
+    }
+    if (REDUCE) block_partials<2>(acc, a.partials);
+}
+
+// f = f^eq(rho0, 0) = w rho0, i.e. h = 0 (collision leaves it unchanged); f* = 0
+template <class L, typename T, typename TA, typename R>
+__global__ void k_flow_init(FlowArgs<T, TA, R> a, int which) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= a.np) return;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        if (which == 0)
+            a.fout[(size_t)i * a.np + n] = Pop<T>::enc(R(0), R(0));
+        else
+            a.aout[(size_t)i * a.np + n] = Pop<TA>::enc(R(0), R(0));
+    }
+    if (which == 0) {  // fields of the initial state f = f^eq(rho0, 0)
+        a.out0[n] = a.rho0;
+        a.out1[n] = R(0);
+        a.out1[a.np + n] = R(0);
+        a.out1[2 * a.np + n] = R(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint kernels
+// ---------------------------------------------------------------------------
+// adjoint moments of f*_S: A = sum w f*, M = sum w f* e, Qm = sum w f* e e^T
+template <class L, typename R>
+struct AdjMoments {
+    R A, M0, M1, M2, Q00, Q11, Q22, Q01, Q02, Q12;
+    __device__ __forceinline__ void compute(const R (&s)[L::Q]) {
+        A = M0 = M1 = M2 = Q00 = Q11 = Q22 = Q01 = Q02 = Q12 = R(0);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const R ws = R(L::w(i)) * s[i];
+            const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+            A += ws;
+            if (x) { M0 += R(x) * ws; Q00 += ws; }
+            if (y) { M1 += R(y) * ws; Q11 += ws; }
+            if (z) { M2 += R(z) * ws; Q22 += ws; }
+            if (x * y) Q01 += R(x * y) * ws;
+            if (x * z) Q02 += R(x * z) * ws;
+            if (y * z) Q12 += R(y * z) * ws;
+        }
+    }
+};
+
+template <class L, typename T, typename TA, typename R>
+__device__ __forceinline__ void pull_adjoint(const FlowArgs<T, TA, R>& a, const Cell& c, R (&s)[L::Q]) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const long long src = shifted<L>(c, i, +1, a.nx, a.ny, a.nz);
+        s[i] = Pop<TA>::ld(a.ain, (size_t)i * a.np + src, R(0)) * a.ascale;
+    }
+}
+
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
+__global__ void __launch_bounds__(256) k_flow_adjoint(FlowArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    double acc[1] = {0.0};
+    if (c.active) {
+        R s[L::Q];
+        pull_adjoint<L>(a, c, s);
+        const int fl = a.flags[c.n];
+        const int type = fl & 7;
+        if (type == WALL) {
+            bounce<L>(s);  // C^T = I, B^T = the same swap
+        } else {
+            const R g = a.gamma[c.n];
+            const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+            AdjMoments<L, R> m;
+            m.compute(s);
+            const R Qu0 = m.Q00 * u0 + m.Q01 * u1 + m.Q02 * u2;
+            const R Qu1 = m.Q01 * u0 + m.Q11 * u1 + m.Q12 * u2;
+            const R Qu2 = m.Q02 * u0 + m.Q12 * u1 + m.Q22 * u2;
+            // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
+            const R c1 = R(3) * g;
+            const R c2 = a.model == 0 ? R(9) * g * g : R(9) * g;
+            const R c3 = a.model == 0 ? R(3) * g * g : R(3) * g;
+            R w0 = c1 * m.M0 + c2 * Qu0 - c3 * m.A * u0;
+            R w1 = c1 * m.M1 + c2 * Qu1 - c3 * m.A * u1;
+            R w2 = c1 * m.M2 + c2 * Qu2 - c3 * m.A * u2;
+            const R om = a.omega;
+            const R base = om * m.A - (type == VEL ? a.src_in : R(0));
+            R v0 = 0, v1 = 0, v2 = 0;
+            if (THERMAL) {
+                v0 = a.cpl[c.n];
+                v1 = a.cpl[a.np + c.n];
+                v2 = a.cpl[2 * a.np + c.n];
+            }
+            w0 = om * w0 + v0;
+            w1 = om * w1 + v1;
+            w2 = om * w2 + v2;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i)
+                s[i] = (R(1) - om) * s[i] + base + R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
+            if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
+        }
+        const R inv = R(1) / a.ascale;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) Pop<TA>::st(a.aout, (size_t)i * a.np + c.n, s[i] * inv, R(0));
+        if (REDUCE && type != WALL) {
+            double t = 0.0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) t += fabs((double)s[i]);
+            acc[0] = t;
+        }
+    }
+    if (REDUCE) block_partials<1>(acc, a.partials);
+}
+
+// J'(x) = -(1/tau) sum_i f*_S,i d f^eq_i / d gamma (Eq. 66), + thermal part
+template <class L, typename T, typename TA, typename R, bool THERMAL>
+__global__ void __launch_bounds__(256) k_flow_sens(FlowArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    if (!c.active) return;
+    const int type = a.flags[c.n] & 7;
+    if (type == WALL) {
+        a.out0[c.n] = R(0);
+        return;
+    }
+    R s[L::Q];
+    pull_adjoint<L>(a, c, s);
+    const R g = a.gamma[c.n];
+    const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+    AdjMoments<L, R> m;
+    m.compute(s);
+    const R Mu = m.M0 * u0 + m.M1 * u1 + m.M2 * u2;
+    const R uQu = m.Q00 * u0 * u0 + m.Q11 * u1 * u1 + m.Q22 * u2 * u2 +
+                  R(2) * (m.Q01 * u0 * u1 + m.Q02 * u0 * u2 + m.Q12 * u1 * u2);
+    const R uu = u0 * u0 + u1 * u1 + u2 * u2;
+    R br;
+    if (a.model == 0)
+        br = R(3) * Mu + R(9) * g * uQu - R(3) * g * uu * m.A;
+    else
+        br = R(3) * Mu + R(4.5) * uQu - R(1.5) * uu * m.A;
+    R out = -a.rho0 * a.omega * br;
+    if (THERMAL) out += a.sT[c.n];
+    a.out0[c.n] = out;
+}
+
+// ---------------------------------------------------------------------------
+// temperature lattice (D3Q7), velocity frozen from the converged flow
+//   g^eq_k = w_k T (1 + 4 e_k.(gamma u)),  tau_g = 1/2 + 4 kappa_f (gamma + (1-gamma) k_r)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R tau_g(R g, R kappa_f, R k_ratio) {
+    return R(0.5) + R(4) * kappa_f * (g + (R(1) - g) * k_ratio);
+}
+
+template <typename R>
+__device__ __forceinline__ R ecomp(int k, R u0, R u1, R u2) {  // e_k . u for D3Q7
+    return R(D3Q7::cx(k)) * u0 + R(D3Q7::cy(k)) * u1 + R(D3Q7::cz(k)) * u2;
+}
+
+// thermal boundary operator: wall bounce-back (+ heat flux), Dirichlet inlet,
+// outflow setting the unknown to its equilibrium share of the node's own T
+template <typename R>
+__device__ __forceinline__ void thermal_bc(R (&g)[7], int fl, const R* __restrict__ bc, R gam,
+                                           R u0, R u1, R u2, R q) {
+    const int type = fl & 7;
+    if (type == FLUID) return;
+    const int kn = ((fl >> 3) & 7) + 1;  // D3Q7 index of the inward normal
+    if (type == WALL) {
+        bounce<D3Q7>(g);
+        if (fl & HEAT_BIT) {
+#pragma unroll
+            for (int k = 1; k < 7; ++k)
+                if (k == kn) g[k] += q;
+        }
+        return;
+    }
+    R K = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        if (k != kn) K += g[k];
+    R val;
+    if (type == VEL) {
+        val = bc[3] - K;
+    } else {
+        R en = 0;
+#pragma unroll
+        for (int k = 1; k < 7; ++k)
+            if (k == kn) en = ecomp<R>(k, u0, u1, u2);
+        const R wa = R(0.125) * (R(1) + R(4) * gam * en);
+        val = wa * K / (R(1) - wa);
+    }
+#pragma unroll
+    for (int k = 1; k < 7; ++k)
+        if (k == kn) g[k] = val;
+}
+
+template <typename T, typename TA, typename R>
+__device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const Cell& c, R (&g)[7],
+                                            R& gam, R& u0, R& u1, R& u2) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const long long src = shifted<D3Q7>(c, k, -1, a.nx, a.ny, a.nz);
+        g[k] = Pop<T>::ld(a.gin, (size_t)k * a.np + src, R(D3Q7::w(k)) * a.T0);
+    }
+    const int fl = a.flags[c.n];
+    gam = a.gamma[c.n];
+    u0 = a.u[c.n];
+    u1 = a.u[a.np + c.n];
+    u2 = a.u[2 * a.np + c.n];
+    thermal_bc<R>(g, fl, a.bc + 4 * c.n, gam, u0, u1, u2, a.q);
+    return fl;
+}
+
+template <typename T, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_thermal_step(ThermArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    double acc[1] = {0.0};
+    if (c.active) {
+        R g[7], gam, u0, u1, u2;
+        const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
+        R tem = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) tem += g[k];
+        if (REDUCE) {  // temperature and frozen post-boundary g of this state
+            a.out0[c.n] = tem;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + c.n] = g[k];
+        }
+        if ((fl & 7) != WALL) {
+            if (REDUCE) acc[0] = (double)tem;
+            const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
+            const R g4 = R(4) * gam;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const R geq = R(D3Q7::w(k)) * tem * (R(1) + g4 * ecomp<R>(k, u0, u1, u2));
+                g[k] += om * (geq - g[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);
+    }
+    if (REDUCE) block_partials<1>(acc, a.partials);
+}
+
+template <typename T, typename TA, typename R>
+__global__ void k_thermal_init(ThermArgs<T, TA, R> a, int which) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= a.np) return;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        if (which == 0)
+            a.gout[(size_t)k * a.np + n] = Pop<T>::enc(R(D3Q7::w(k)) * a.T0, R(D3Q7::w(k)) * a.T0);
+        else
+            a.aout[(size_t)k * a.np + n] = Pop<TA>::enc(R(0), R(0));
+    }
+    if (which == 0) {
+        a.out0[n] = a.T0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + n] = R(D3Q7::w(k)) * a.T0;
+    } else {
+        a.gcn[n] = R(0);
+    }
+}
+
+// adjoint of the thermal collision at one node:
+//   g*_C,l = (1 - 1/tau_g) g*_S,l + (1/tau_g) sum_k w_k a_k g*_S,k - dJ/dg_l
+template <typename R>
+__device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, R u1, R u2, R om, R src) {
+    R B = 0;
+    const R g4 = R(4) * gam;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) B += R(D3Q7::w(k)) * (R(1) + g4 * ecomp<R>(k, u0, u1, u2)) * s[k];
+    const R base = om * B - src;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) s[k] = (R(1) - om) * s[k] + base;
+}
+
+template <typename T, typename TA, typename R>
+__device__ __forceinline__ void thermal_pull_adjoint(const ThermArgs<T, TA, R>& a, const Cell& c, R (&s)[7]) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const long long src = shifted<D3Q7>(c, k, +1, a.nx, a.ny, a.nz);
+        s[k] = Pop<TA>::ld(a.ain, (size_t)k * a.np + src, R(0)) * a.ascale;
+    }
+}
+
+template <typename T, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    double acc[1] = {0.0};
+    if (c.active) {
+        R s[7];
+        thermal_pull_adjoint(a, c, s);
+        const int fl = a.flags[c.n];
+        const int type = fl & 7;
+        if (type == WALL) {
+            bounce<D3Q7>(s);
+        } else {
+            const R gam = a.gamma[c.n];
+            const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+            const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
+            thermal_adjoint_collide<R>(s, gam, u0, u1, u2, om, a.src_T);
+            if (type >= VEL) {
+                const int kn = ((fl >> 3) & 7) + 1;
+                R ckn = 0, en = 0;
+#pragma unroll
+                for (int k = 1; k < 7; ++k)
+                    if (k == kn) {
+                        ckn = s[k];
+                        en = ecomp<R>(k, u0, u1, u2);
+                    }
+                R coef;
+                if (type == VEL) {
+                    coef = R(-1);
+                } else {
+                    const R wa = R(0.125) * (R(1) + R(4) * gam * en);
+                    coef = wa / (R(1) - wa);
+                    a.gcn[c.n] = ckn;
+                }
+#pragma unroll
+                for (int k = 0; k < 7; ++k) s[k] = (k == kn) ? R(0) : s[k] + coef * ckn;
+            }
+        }
+        const R inv = R(1) / a.ascale;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) Pop<TA>::st(a.aout, (size_t)k * a.np + c.n, s[k] * inv, R(0));
+        if (REDUCE && type != WALL) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) t += fabs((double)s[k]);
+            acc[0] = t;
+        }
+    }
+    if (REDUCE) block_partials<1>(acc, a.partials);
+}
+
+// thermal-to-flow coupling v/rho0 (added as e_i.v/rho0 to f*_C,i) and the
+// thermal part of dJ/dgamma, from the current thermal adjoint iterate:
+//   v   = (4 gamma T / tau_g) sum_k w_k g*_S,k e_k
+//         + [outlet] g*_C,n w K/(1 - w a)^2 4 gamma e_n
+//   s_T = -sum_k g*_S,k d g_C,k/d gamma - [outlet] g*_C,n w K/(1 - w a)^2 4 e_n.u
+// The outlet terms linearise the boundary operator at the post-stream state of
+// the stored temperature iterate (K = sum of its known post-stream
+// populations), the same point as the collision terms.
+template <typename T, typename TA, typename R>
+__global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    if (!c.active) return;
+    const int fl = a.flags[c.n];
+    const int type = fl & 7;
+    R v0 = 0, v1 = 0, v2 = 0, sT = 0;
+    if (type != WALL) {
+        R s[7];
+        thermal_pull_adjoint(a, c, s);
+        const R gam = a.gamma[c.n];
+        const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+        R gp[7], tem = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            gp[k] = a.gpost[(size_t)k * a.np + c.n];
+            tem += gp[k];
+        }
+        const R tg = tau_g<R>(gam, a.kappa_f, a.k_ratio);
+        const R om = R(1) / tg;
+        const R dom = -R(4) * a.kappa_f * (R(1) - a.k_ratio) * om * om;  // d(1/tau_g)/d gamma
+        R Mg0 = 0, Mg1 = 0, Mg2 = 0, s1 = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const R ws = R(D3Q7::w(k)) * s[k];
+            Mg0 += R(D3Q7::cx(k)) * ws;
+            Mg1 += R(D3Q7::cy(k)) * ws;
+            Mg2 += R(D3Q7::cz(k)) * ws;
+            const R eu = ecomp<R>(k, u0, u1, u2);
+            const R geq = R(D3Q7::w(k)) * tem * (R(1) + R(4) * gam * eu);
+            s1 += s[k] * (-(gp[k] - geq) * dom + om * R(D3Q7::w(k)) * tem * R(4) * eu);
+        }
+        const R cf = R(4) * gam * tem * om;
+        v0 = cf * Mg0;
+        v1 = cf * Mg1;
+        v2 = cf * Mg2;
+        sT = -s1;
+        if (type == PRES) {
+            const int kn = ((fl >> 3) & 7) + 1;
+            R en = 0;
+#pragma unroll
+            for (int k = 1; k < 7; ++k)
+                if (k == kn) en = ecomp<R>(k, u0, u1, u2);
+            const R wa = R(0.125) * (R(1) + R(4) * gam * en);
+            R K = 0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                if (k == kn) continue;
+                const long long src = shifted<D3Q7>(c, k, -1, a.nx, a.ny, a.nz);
+                K += Pop<T>::ld(a.gin, (size_t)k * a.np + src, R(D3Q7::w(k)) * a.T0);
+            }
+            const R dgda = R(0.125) * K / ((R(1) - wa) * (R(1) - wa));
+            const R ckn = a.gcn[c.n];
+            const R cb = ckn * dgda * R(4) * gam;
+            v0 += cb * R(D3Q7::cx(kn));
+            v1 += cb * R(D3Q7::cy(kn));
+            v2 += cb * R(D3Q7::cz(kn));
+            sT -= ckn * dgda * R(4) * en;
+        }
+    }
+    const R inv = R(1) / a.rho0;
+    a.out0[c.n] = v0 * inv;
+    a.out0[a.np + c.n] = v1 * inv;
+    a.out0[2 * a.np + c.n] = v2 * inv;
+    a.out1[c.n] = sT;
+}
+
+// deterministic second stage of every reduction: one block sums the per-block
+// partials in a fixed order
+template <int NV>
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, long long nblocks,
+                                                  double* __restrict__ out) {
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += partials[b * NV + k];
+    __shared__ double sh[NV][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = s[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[k][warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < (int)(blockDim.x >> 5) ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) out[k] = t;
+        }
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,90 @@
+// lbm_internal.h -- type-erased launch interface between the C-ABI runtime
+// and the templated kernels (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+struct Geom {
+    dim3 grid;
+    dim3 block;
+    long long nblocks;  // grid.x * grid.y * grid.z (reduction partial count)
+};
+
+// (BX x BY) tiles of x-y planes, one thread per node, 256 threads when the
+// lattice is wide enough; BX divides nx when possible so no lane idles.
+Geom make_geom(int nx, int ny, int nz);
+
+struct FlowLaunch {
+    const void* fin;
+    void* fout;
+    const void* ain;
+    void* aout;
+    const uint8_t* flags;
+    const void* gamma;
+    const void* bc;
+    const void* u;
+    const void* cpl;
+    const void* sT;
+    void* out0;
+    void* out1;
+    double* partials;
+    int nx, ny, nz;
+    long long np;
+    double omega, rho0, src_in, ascale;
+    int model;
+};
+
+struct ThermLaunch {
+    const void* gin;
+    void* gout;
+    const void* ain;
+    void* aout;
+    const uint8_t* flags;
+    const void* gamma;
+    const void* bc;
+    const void* u;
+    const void* gpost;
+    void* gcn;
+    void* out0;
+    void* out1;
+    double* partials;
+    int nx, ny, nz;
+    long long np;
+    double rho0, kappa_f, k_ratio, q, T0, src_T, ascale;
+};
+
+enum FlowOp {
+    FOP_INIT_F = 0,
+    FOP_INIT_A,
+    FOP_STEP,
+    FOP_STEP_RED,
+    FOP_ADJ,
+    FOP_ADJ_RED,
+    FOP_ADJ_T,
+    FOP_ADJ_T_RED,
+    FOP_SENS,
+    FOP_SENS_T
+};
+
+enum ThermOp { TOP_INIT_G = 0, TOP_INIT_A, TOP_STEP, TOP_STEP_RED, TOP_ADJ, TOP_ADJ_RED, TOP_COUPLING };
+
+// storage codes follow lbm_storage; stencil codes follow lbm_stencil
+cudaError_t flow_launch(int stencil, int storage, FlowOp op, const FlowLaunch& a, const Geom& g,
+                        cudaStream_t s);
+cudaError_t thermal_launch(int storage, ThermOp op, const ThermLaunch& a, const Geom& g,
+                           cudaStream_t s);
+cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, double* out,
+                            cudaStream_t s);
+// element conversion between float/double buffers (device to device)
+cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64, long long n,
+                           cudaStream_t s);
+
+// bytes per stored population / adjoint population / auxiliary value
+size_t pop_bytes(int storage);
+size_t adj_bytes(int storage);
+size_t aux_bytes(int storage);
+
+}  // namespace lbm

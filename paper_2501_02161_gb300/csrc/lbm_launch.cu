@@ -1,0 +1,203 @@
+// lbm_launch.cu -- template instantiation and dispatch of the kernels for each
+// (stencil, storage) pair.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+Geom make_geom(int nx, int ny, int nz) {
+    Geom g;
+    int bx = (nx % 128 == 0) ? 128 : ((nx % 64 == 0 || nx > 96) ? 64 : 32);
+    int by = 256 / bx;
+    if (by > ny) by = ny;
+    if (by < 1) by = 1;
+    g.block = dim3(bx, by, 1);
+    g.grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+    g.nblocks = (long long)g.grid.x * g.grid.y * g.grid.z;
+    return g;
+}
+
+namespace {
+
+template <typename T> struct Types;
+// storage -> (population type, adjoint type, compute type)
+template <int S> struct StorageTypes;
+template <> struct StorageTypes<0> { using T = double; using TA = double; using R = double; };
+template <> struct StorageTypes<1> { using T = float; using TA = float; using R = float; };
+template <> struct StorageTypes<2> { using T = __half; using TA = float; using R = float; };
+template <> struct StorageTypes<3> { using T = __nv_bfloat16; using TA = float; using R = float; };
+
+template <int S>
+FlowArgs<typename StorageTypes<S>::T, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
+flow_args(const FlowLaunch& l) {
+    using T = typename StorageTypes<S>::T;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    FlowArgs<T, TA, R> a;
+    a.fin = (const T*)l.fin;
+    a.fout = (T*)l.fout;
+    a.ain = (const TA*)l.ain;
+    a.aout = (TA*)l.aout;
+    a.flags = l.flags;
+    a.gamma = (const R*)l.gamma;
+    a.bc = (const R*)l.bc;
+    a.u = (const R*)l.u;
+    a.cpl = (const R*)l.cpl;
+    a.sT = (const R*)l.sT;
+    a.out0 = (R*)l.out0;
+    a.out1 = (R*)l.out1;
+    a.partials = l.partials;
+    a.nx = l.nx;
+    a.ny = l.ny;
+    a.nz = l.nz;
+    a.np = l.np;
+    a.omega = (R)l.omega;
+    a.rho0 = (R)l.rho0;
+    a.src_in = (R)l.src_in;
+    a.ascale = (R)l.ascale;
+    a.model = l.model;
+    return a;
+}
+
+template <int S>
+ThermArgs<typename StorageTypes<S>::T, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
+therm_args(const ThermLaunch& l) {
+    using T = typename StorageTypes<S>::T;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    ThermArgs<T, TA, R> a;
+    a.gin = (const T*)l.gin;
+    a.gout = (T*)l.gout;
+    a.ain = (const TA*)l.ain;
+    a.aout = (TA*)l.aout;
+    a.flags = l.flags;
+    a.gamma = (const R*)l.gamma;
+    a.bc = (const R*)l.bc;
+    a.u = (const R*)l.u;
+    a.gpost = (const R*)l.gpost;
+    a.gcn = (R*)l.gcn;
+    a.out0 = (R*)l.out0;
+    a.out1 = (R*)l.out1;
+    a.partials = l.partials;
+    a.nx = l.nx;
+    a.ny = l.ny;
+    a.nz = l.nz;
+    a.np = l.np;
+    a.rho0 = (R)l.rho0;
+    a.kappa_f = (R)l.kappa_f;
+    a.k_ratio = (R)l.k_ratio;
+    a.q = (R)l.q;
+    a.T0 = (R)l.T0;
+    a.src_T = (R)l.src_T;
+    a.ascale = (R)l.ascale;
+    return a;
+}
+
+inline dim3 flat_grid(long long np) { return dim3((unsigned)((np + 255) / 256)); }
+
+template <class L, int S>
+void flow_dispatch(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t s) {
+    using T = typename StorageTypes<S>::T;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    auto a = flow_args<S>(l);
+    switch (op) {
+        case FOP_INIT_F: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
+        case FOP_INIT_A: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
+        case FOP_STEP: k_flow_step<L, T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_STEP_RED: k_flow_step<L, T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_ADJ: k_flow_adjoint<L, T, TA, R, false, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_ADJ_RED: k_flow_adjoint<L, T, TA, R, true, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_ADJ_T: k_flow_adjoint<L, T, TA, R, false, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_ADJ_T_RED: k_flow_adjoint<L, T, TA, R, true, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_SENS: k_flow_sens<L, T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_SENS_T: k_flow_sens<L, T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
+    }
+}
+
+template <int S>
+void therm_dispatch(ThermOp op, const ThermLaunch& l, const Geom& g, cudaStream_t s) {
+    using T = typename StorageTypes<S>::T;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    auto a = therm_args<S>(l);
+    switch (op) {
+        case TOP_INIT_G: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
+        case TOP_INIT_A: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
+        case TOP_STEP: k_thermal_step<T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_STEP_RED: k_thermal_step<T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_ADJ: k_thermal_adjoint<T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_ADJ_RED: k_thermal_adjoint<T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_COUPLING: k_thermal_coupling<T, TA, R><<<g.grid, g.block, 0, s>>>(a); break;
+    }
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (D)src[i];
+}
+
+}  // namespace
+
+cudaError_t flow_launch(int stencil, int storage, FlowOp op, const FlowLaunch& a, const Geom& g,
+                        cudaStream_t s) {
+    if (stencil == 0) {
+        switch (storage) {
+            case 0: flow_dispatch<D2Q9, 0>(op, a, g, s); break;
+            case 1: flow_dispatch<D2Q9, 1>(op, a, g, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (storage) {
+            case 0: flow_dispatch<D3Q19, 0>(op, a, g, s); break;
+            case 1: flow_dispatch<D3Q19, 1>(op, a, g, s); break;
+            case 2: flow_dispatch<D3Q19, 2>(op, a, g, s); break;
+            case 3: flow_dispatch<D3Q19, 3>(op, a, g, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t thermal_launch(int storage, ThermOp op, const ThermLaunch& a, const Geom& g,
+                           cudaStream_t s) {
+    switch (storage) {
+        case 0: therm_dispatch<0>(op, a, g, s); break;
+        case 1: therm_dispatch<1>(op, a, g, s); break;
+        case 2: therm_dispatch<2>(op, a, g, s); break;
+        case 3: therm_dispatch<3>(op, a, g, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, double* out,
+                            cudaStream_t s) {
+    if (nv == 1)
+        k_finalize<1><<<1, 256, 0, s>>>(partials, nblocks, out);
+    else
+        k_finalize<2><<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64, long long n,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + 255) / 256));
+    if (src_f64 && dst_f64)
+        return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (!src_f64 && !dst_f64)
+        return cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (src_f64)
+        k_convert<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)dst, n);
+    else
+        k_convert<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)dst, n);
+    return cudaGetLastError();
+}
+
+size_t pop_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
+size_t adj_bytes(int storage) { return storage == 0 ? 8 : 4; }
+size_t aux_bytes(int storage) { return storage == 0 ? 8 : 4; }
+
+}  // namespace lbm

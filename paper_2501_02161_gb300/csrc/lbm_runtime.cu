@@ -1,0 +1,755 @@
+// lbm_runtime.cu -- the C-ABI (include/lbmadj.h): context, device buffers,
+// convergence loops and result read-back.
+//
+// Each solve phase runs in blocks of K steps.  A block is captured once as a
+// CUDA graph (K-1 plain fused steps, one reducing step, the deterministic
+// finalize kernel and the copy of the sums to pinned host memory) and then
+// replayed, so a block costs one graph launch and one host synchronisation.
+// The residual |I(t) - I(t-K)| / |I(t)| is evaluated on the host from the FP64
+// sums (Sec. 3.1, Fig. 8 text).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbmadj.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return fail(_e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,    \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));             \
+    } while (0)
+
+enum Phase { PH_FLOW = 0, PH_THERM = 1, PH_ADJ = 2, PH_TADJ = 3 };
+
+}  // namespace
+
+struct lbm_ctx {
+    int device = 0;
+    int stencil = 1, Q = 19, storage = 1;
+    bool thermal = false;
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0, np = 0;
+    size_t pb = 4, ab = 4, rb = 4;  // population / adjoint / aux element bytes
+
+    cudaStream_t stream = nullptr;  // internal work stream
+    cudaStream_t user = nullptr;    // caller's stream (ordering only)
+    cudaEvent_t ev = nullptr;
+
+    void* f[2] = {nullptr, nullptr};
+    void* fa[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    void* ga[2] = {nullptr, nullptr};
+    int fcur = 0, facur = 0, gcur = 0, gacur = 0;
+
+    uint8_t* flags = nullptr;
+    void* gamma = nullptr;
+    void* bc = nullptr;
+    void* u = nullptr;      // 3 planes
+    void* rho = nullptr;
+    void* T = nullptr;
+    void* gpost = nullptr;  // 7 planes
+    void* cpl = nullptr;    // 3 planes
+    void* sT = nullptr;
+    void* gcn = nullptr;
+    void* sens = nullptr;
+    double* partials = nullptr;
+    double* dres = nullptr;
+    double* hres = nullptr;  // pinned, 4 doubles
+
+    Geom geom{};
+    lbm_params prm{0.6, 1.0, 0, 0.0, 1.0, 0.0, 0.0};
+    lbm_objective obj{1.0, 0.0};
+    long long n_in = 0, n_nw = 0;
+    bool have_flags = false, have_gamma = false, have_bc = false, have_params = false;
+    bool fwd_done = false, adj_done = false;
+    double J_p = 0.0, J_T = 0.0;
+    double last_I[4] = {0, 0, 0, 0};
+
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+
+    void drop_graphs() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+    }
+};
+
+namespace {
+
+void* dalloc(size_t bytes, cudaError_t* err) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    return e == cudaSuccess ? p : nullptr;
+}
+
+void free_all(lbm_ctx* c) {
+    c->drop_graphs();
+    void* bufs[] = {c->f[0], c->f[1], c->fa[0], c->fa[1], c->g[0], c->g[1], c->ga[0], c->ga[1],
+                    c->flags, c->gamma, c->bc, c->u, c->rho, c->T, c->gpost, c->cpl, c->sT,
+                    c->gcn, c->sens, c->partials, c->dres};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (c->hres) cudaFreeHost(c->hres);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+// order ctx work after the caller's stream, and the caller's stream after it
+lbm_status enter(lbm_ctx* c) {
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaEventRecord(c->ev, c->user));
+    CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev, 0));
+    return LBM_OK;
+}
+
+lbm_status leave(lbm_ctx* c) {
+    CUDA_TRY(cudaEventRecord(c->ev, c->stream));
+    CUDA_TRY(cudaStreamWaitEvent(c->user, c->ev, 0));
+    return LBM_OK;
+}
+
+FlowLaunch flow_base(lbm_ctx* c) {
+    FlowLaunch a;
+    std::memset(&a, 0, sizeof(a));
+    a.flags = c->flags;
+    a.gamma = c->gamma;
+    a.bc = c->bc;
+    a.u = c->u;
+    a.cpl = c->cpl;
+    a.sT = c->sT;
+    a.partials = c->partials;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    a.np = c->np;
+    a.omega = 1.0 / c->prm.tau;
+    a.rho0 = c->prm.rho0;
+    a.src_in = c->n_in > 0 ? c->obj.w_pin / (3.0 * (double)c->n_in) : 0.0;
+    a.ascale = 1.0;
+    a.model = c->prm.gamma_model;
+    return a;
+}
+
+ThermLaunch therm_base(lbm_ctx* c) {
+    ThermLaunch a;
+    std::memset(&a, 0, sizeof(a));
+    a.flags = c->flags;
+    a.gamma = c->gamma;
+    a.bc = c->bc;
+    a.u = c->u;
+    a.gpost = c->gpost;
+    a.gcn = c->gcn;
+    a.partials = c->partials;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    a.np = c->np;
+    a.rho0 = c->prm.rho0;
+    a.kappa_f = c->prm.kappa_f;
+    a.k_ratio = c->prm.k_ratio;
+    a.q = c->prm.q_flux;
+    a.T0 = c->prm.T0;
+    a.src_T = c->n_nw > 0 ? c->obj.w_tmean / (double)c->n_nw : 0.0;
+    a.ascale = 1.0;
+    return a;
+}
+
+int phase_nv(int ph) { return ph == PH_FLOW ? 2 : 1; }
+
+// enqueue one step of a phase on stream s; the reducing variant writes the
+// per-block partial sums (and the fields of the post-boundary state)
+cudaError_t enqueue_step(lbm_ctx* c, int ph, bool reduce, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (ph == PH_FLOW) {
+        FlowLaunch a = flow_base(c);
+        a.fin = c->f[c->fcur];
+        a.fout = c->f[1 - c->fcur];
+        a.out0 = c->rho;
+        a.out1 = c->u;
+        e = flow_launch(c->stencil, c->storage, reduce ? FOP_STEP_RED : FOP_STEP, a, c->geom, s);
+        c->fcur ^= 1;
+    } else if (ph == PH_THERM) {
+        ThermLaunch a = therm_base(c);
+        a.gin = c->g[c->gcur];
+        a.gout = c->g[1 - c->gcur];
+        a.out0 = c->T;
+        a.out1 = c->gpost;
+        e = thermal_launch(c->storage, reduce ? TOP_STEP_RED : TOP_STEP, a, c->geom, s);
+        c->gcur ^= 1;
+    } else if (ph == PH_ADJ) {
+        FlowLaunch a = flow_base(c);
+        a.ain = c->fa[c->facur];
+        a.aout = c->fa[1 - c->facur];
+        FlowOp op = c->thermal ? (reduce ? FOP_ADJ_T_RED : FOP_ADJ_T) : (reduce ? FOP_ADJ_RED : FOP_ADJ);
+        e = flow_launch(c->stencil, c->storage, op, a, c->geom, s);
+        c->facur ^= 1;
+    } else {
+        ThermLaunch a = therm_base(c);
+        a.ain = c->ga[c->gacur];
+        a.aout = c->ga[1 - c->gacur];
+        e = thermal_launch(c->storage, reduce ? TOP_ADJ_RED : TOP_ADJ, a, c->geom, s);
+        c->gacur ^= 1;
+    }
+    return e;
+}
+
+int& parity_of(lbm_ctx* c, int ph) {
+    return ph == PH_FLOW ? c->fcur : (ph == PH_THERM ? c->gcur : (ph == PH_ADJ ? c->facur : c->gacur));
+}
+
+// enqueue a block of k steps ending with a reduction, the finalize kernel and
+// the copy of the sums to c->hres
+cudaError_t enqueue_block(lbm_ctx* c, int ph, int k, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < k && e == cudaSuccess; ++i) e = enqueue_step(c, ph, i == k - 1, s);
+    if (e != cudaSuccess) return e;
+    e = finalize_launch(c->partials, c->geom.nblocks, phase_nv(ph), c->dres, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * phase_nv(ph), cudaMemcpyDeviceToHost, s);
+}
+
+lbm_status run_block(lbm_ctx* c, int ph, int k) {
+    int& par = parity_of(c, ph);
+    auto key = std::make_tuple(ph, k, par);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        int par0 = par;
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_block(c, ph, k, c->stream);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+        par = par0;  // capture only recorded the work
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            return fail(LBM_ERR_CUDA, std::string("graph capture failed: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+        it = c->graphs.emplace(key, exec).first;
+    }
+    CUDA_TRY(cudaGraphLaunch(it->second, c->stream));
+    if (k % 2) par ^= 1;
+    return LBM_OK;
+}
+
+double rel_change(double cur, double prev) {
+    double d = std::fabs(cur - prev);
+    if (d == 0.0) return 0.0;
+    return cur != 0.0 ? d / std::fabs(cur) : INFINITY;
+}
+
+// run a phase to tolerance (or a fixed number of steps when tol <= 0)
+lbm_status run_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, long long* steps_out,
+                     double* res_out, double* I_out) {
+    const int K = o->check_every;
+    long long steps = 0;
+    double res = INFINITY;
+    double prev = c->last_I[ph];
+    double cur = prev;
+    while (steps < o->max_steps) {
+        long long k = std::min<long long>(K, o->max_steps - steps);
+        lbm_status st = run_block(c, ph, (int)k);
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        steps += k;
+        double denom = (double)(c->n_nw > 0 ? c->n_nw : 1);
+        cur = c->hres[0] / denom;
+        if (ph == PH_FLOW)
+            c->J_p = c->n_in > 0 ? c->obj.w_pin * c->hres[1] / (3.0 * (double)c->n_in) : 0.0;
+        if (ph == PH_THERM) c->J_T = c->obj.w_tmean * cur;
+        if (!std::isfinite(cur) || (ph == PH_FLOW && !std::isfinite(c->hres[1]))) {
+            *steps_out = steps;
+            *res_out = NAN;
+            *I_out = cur;
+            c->last_I[ph] = cur;
+            return fail(LBM_ERR_DIVERGED, "non-finite residual quantity after " +
+                                              std::to_string(steps) + " steps");
+        }
+        res = rel_change(cur, prev);
+        prev = cur;
+        if (o->tol > 0 && res < o->tol) break;
+    }
+    c->last_I[ph] = cur;
+    *steps_out = steps;
+    *res_out = res;
+    *I_out = cur;
+    if (o->tol > 0 && !(res < o->tol)) return LBM_NOT_CONVERGED;
+    return LBM_OK;
+}
+
+lbm_status check_opts(const lbm_solve_opts* o) {
+    if (!o) return fail(LBM_ERR_ARG, "opts is null");
+    if (o->max_steps < 0) return fail(LBM_ERR_ARG, "max_steps < 0");
+    if (o->check_every <= 0) return fail(LBM_ERR_ARG, "check_every must be > 0");
+    if (std::isnan(o->tol)) return fail(LBM_ERR_ARG, "tol is NaN");
+    return LBM_OK;
+}
+
+lbm_status ready(lbm_ctx* c) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    if (!c->have_flags) return fail(LBM_ERR_ORDER, "lbm_set_flags has not been called");
+    if (!c->have_gamma) return fail(LBM_ERR_ORDER, "lbm_set_gamma has not been called");
+    if (!c->have_bc) return fail(LBM_ERR_ORDER, "lbm_set_bc_values has not been called");
+    if (!c->have_params) return fail(LBM_ERR_ORDER, "lbm_set_params has not been called");
+    return LBM_OK;
+}
+
+// copy n values of dtype (host or device) into the ctx aux buffer dst (R type)
+lbm_status copy_in(lbm_ctx* c, void* dst, const void* src, size_t n, int dtype, int on_device) {
+    const bool r64 = c->rb == 8;
+    const bool s64 = dtype == LBM_DTYPE_F64;
+    if (on_device) {
+        CUDA_TRY(convert_launch(src, s64, dst, r64, (long long)n, c->stream));
+    } else if (s64 == r64) {
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n * c->rb, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<char> tmp(n * c->rb);
+        for (size_t i = 0; i < n; ++i) {
+            double v = s64 ? ((const double*)src)[i] : (double)((const float*)src)[i];
+            if (r64)
+                ((double*)tmp.data())[i] = v;
+            else
+                ((float*)tmp.data())[i] = (float)v;
+        }
+        CUDA_TRY(cudaMemcpyAsync(dst, tmp.data(), n * c->rb, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+// copy nplanes planes of N values (stride np) out of an aux buffer
+lbm_status copy_out(lbm_ctx* c, void* dst, const void* src, int nplanes, int dtype, int on_device) {
+    const bool r64 = c->rb == 8;
+    const bool d64 = dtype == LBM_DTYPE_F64;
+    const size_t db = d64 ? 8 : 4;
+    if (on_device) {
+        for (int p = 0; p < nplanes; ++p)
+            CUDA_TRY(convert_launch((const char*)src + p * c->np * c->rb, r64,
+                                    (char*)dst + p * c->N * db, d64, c->N, c->stream));
+    } else {
+        std::vector<char> tmp(c->N * c->rb);
+        for (int p = 0; p < nplanes; ++p) {
+            CUDA_TRY(cudaMemcpyAsync(tmp.data(), (const char*)src + p * c->np * c->rb, c->N * c->rb,
+                                     cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (long long i = 0; i < c->N; ++i) {
+                double v = r64 ? ((double*)tmp.data())[i] : (double)((float*)tmp.data())[i];
+                if (d64)
+                    ((double*)dst)[p * c->N + i] = v;
+                else
+                    ((float*)dst)[p * c->N + i] = (float)v;
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status init_forward(lbm_ctx* c) {
+    FlowLaunch a = flow_base(c);
+    a.fout = c->f[0];
+    a.out0 = c->rho;
+    a.out1 = c->u;
+    c->fcur = 0;
+    CUDA_TRY(flow_launch(c->stencil, c->storage, FOP_INIT_F, a, c->geom, c->stream));
+    c->last_I[PH_FLOW] = 0.0;
+    if (c->thermal) {
+        ThermLaunch t = therm_base(c);
+        t.gout = c->g[0];
+        t.out0 = c->T;
+        t.out1 = c->gpost;
+        c->gcur = 0;
+        CUDA_TRY(thermal_launch(c->storage, TOP_INIT_G, t, c->geom, c->stream));
+        c->last_I[PH_THERM] = c->prm.T0;
+    }
+    return LBM_OK;
+}
+
+lbm_status init_adjoint(lbm_ctx* c) {
+    FlowLaunch a = flow_base(c);
+    a.aout = c->fa[0];
+    c->facur = 0;
+    CUDA_TRY(flow_launch(c->stencil, c->storage, FOP_INIT_A, a, c->geom, c->stream));
+    c->last_I[PH_ADJ] = 0.0;
+    if (c->thermal) {
+        ThermLaunch t = therm_base(c);
+        t.aout = c->ga[0];
+        c->gacur = 0;
+        CUDA_TRY(thermal_launch(c->storage, TOP_INIT_A, t, c->geom, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->cpl, 0, 3 * c->np * c->rb, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->sT, 0, c->np * c->rb, c->stream));
+        c->last_I[PH_TADJ] = 0.0;
+    }
+    return LBM_OK;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+const char* lbm_version(void) { return "lbmadj 0.1 (sm_103a)"; }
+
+lbm_status lbm_create(lbm_ctx** out, int stencil, int nx, int ny, int nz, int storage, int thermal) {
+    if (!out) return fail(LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (stencil != LBM_D2Q9 && stencil != LBM_D3Q19) return fail(LBM_ERR_ARG, "unknown stencil");
+    if (storage < LBM_FP64 || storage > LBM_BF16_OFS) return fail(LBM_ERR_ARG, "unknown storage");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(LBM_ERR_ARG, "lattice sizes must be positive");
+    if (stencil == LBM_D2Q9 && nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
+    if (stencil == LBM_D2Q9 && thermal) return fail(LBM_ERR_UNSUPPORTED, "thermal lattice needs D3Q19");
+    if (stencil == LBM_D2Q9 && storage > LBM_FP32)
+        return fail(LBM_ERR_UNSUPPORTED, "16-bit storage is built for D3Q19 only");
+    if ((long long)nx * ny * nz > (1LL << 31) - 1024) return fail(LBM_ERR_ARG, "lattice too large");
+    lbm_ctx* c = new lbm_ctx();
+    cudaGetDevice(&c->device);
+    c->stencil = stencil;
+    c->Q = stencil == LBM_D2Q9 ? 9 : 19;
+    c->storage = storage;
+    c->thermal = thermal != 0;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (long long)nx * ny * nz;
+    c->np = (c->N + 63) / 64 * 64;
+    c->pb = pop_bytes(storage);
+    c->ab = adj_bytes(storage);
+    c->rb = aux_bytes(storage);
+    c->geom = make_geom(nx, ny, nz);
+    cudaError_t e = cudaSuccess;
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(LBM_ERR_CUDA, std::string("stream/event: ") + cudaGetErrorString(e));
+    }
+    const size_t np = (size_t)c->np;
+    for (int b = 0; b < 2; ++b) {
+        c->f[b] = dalloc(np * c->Q * c->pb, &e);
+        c->fa[b] = dalloc(np * c->Q * c->ab, &e);
+        if (c->thermal) {
+            c->g[b] = dalloc(np * 7 * c->pb, &e);
+            c->ga[b] = dalloc(np * 7 * c->ab, &e);
+        }
+    }
+    c->flags = (uint8_t*)dalloc(np, &e);
+    c->gamma = dalloc(np * c->rb, &e);
+    c->bc = dalloc(np * 4 * c->rb, &e);
+    c->u = dalloc(np * 3 * c->rb, &e);
+    c->rho = dalloc(np * c->rb, &e);
+    c->sens = dalloc(np * c->rb, &e);
+    if (c->thermal) {
+        c->T = dalloc(np * c->rb, &e);
+        c->gpost = dalloc(np * 7 * c->rb, &e);
+        c->cpl = dalloc(np * 3 * c->rb, &e);
+        c->sT = dalloc(np * c->rb, &e);
+        c->gcn = dalloc(np * c->rb, &e);
+    }
+    c->partials = (double*)dalloc(sizeof(double) * 2 * (size_t)c->geom.nblocks, &e);
+    c->dres = (double*)dalloc(sizeof(double) * 4, &e);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->hres, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 1 /* WALL */, np, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bc, 0, np * 4 * c->rb, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->gamma, 0, np * c->rb, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                    std::string("allocation: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* s) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    c->user = (cudaStream_t)s;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_device) {
+    if (!c || !flags) return fail(LBM_ERR_ARG, "null argument");
+    if ((long long)n != c->N) return fail(LBM_ERR_ARG, "flags: n != nx*ny*nz");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    std::vector<uint8_t> h(n);
+    if (on_device) {
+        CUDA_TRY(cudaMemcpyAsync(h.data(), flags, n, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(h.data(), flags, n);
+    }
+    long long nin = 0, nnw = 0;
+    for (size_t i = 0; i < n; ++i) {
+        int fl = h[i], type = fl & 7, code = (fl >> 3) & 7;
+        if (fl & 0x80) return fail(LBM_ERR_ARG, "flag bit 7 set at node " + std::to_string(i));
+        if (type > 3) return fail(LBM_ERR_ARG, "unknown node type at node " + std::to_string(i));
+        if ((type >= 2 || (fl & 0x40)) && (code > 5 || (c->stencil == LBM_D2Q9 && code > 3)))
+            return fail(LBM_ERR_ARG, "bad normal code at node " + std::to_string(i));
+        if ((fl & 0x40) && type != 1) return fail(LBM_ERR_ARG, "HEAT bit on a non-wall node");
+        nin += type == 2;
+        nnw += type != 1;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->flags, h.data(), n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->n_in = nin;
+    c->n_nw = nnw;
+    c->have_flags = true;
+    c->fwd_done = c->adj_done = false;
+    c->drop_graphs();  // objective source depends on N_in / N_nonwall
+    return leave(c);
+}
+
+lbm_status lbm_set_gamma(lbm_ctx* c, const void* gamma, size_t n, int dtype, int on_device) {
+    if (!c || !gamma) return fail(LBM_ERR_ARG, "null argument");
+    if ((long long)n != c->N) return fail(LBM_ERR_ARG, "gamma: n != nx*ny*nz");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    st = copy_in(c, c->gamma, gamma, n, dtype, on_device);
+    if (st != LBM_OK) return st;
+    c->have_gamma = true;
+    c->fwd_done = c->adj_done = false;
+    return leave(c);
+}
+
+lbm_status lbm_set_bc_values(lbm_ctx* c, const void* v, size_t n, int dtype, int on_device) {
+    if (!c || !v) return fail(LBM_ERR_ARG, "null argument");
+    if ((long long)n != 4 * c->N) return fail(LBM_ERR_ARG, "bc values: n != 4*nx*ny*nz");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    st = copy_in(c, c->bc, v, n, dtype, on_device);
+    if (st != LBM_OK) return st;
+    c->have_bc = true;
+    c->fwd_done = c->adj_done = false;
+    return leave(c);
+}
+
+lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
+    if (!c || !p) return fail(LBM_ERR_ARG, "null argument");
+    if (!(p->tau > 0.5)) return fail(LBM_ERR_ARG, "tau must be > 0.5");
+    if (!(p->rho0 > 0)) return fail(LBM_ERR_ARG, "rho0 must be > 0");
+    if (p->gamma_model != LBM_GAMMA_EQ12 && p->gamma_model != LBM_GAMMA_LINEAR)
+        return fail(LBM_ERR_ARG, "unknown gamma model");
+    if (c->thermal && !(p->kappa_f >= 0)) return fail(LBM_ERR_ARG, "kappa_f must be >= 0");
+    if (c->thermal && !(p->k_ratio > 0)) return fail(LBM_ERR_ARG, "k_ratio must be > 0");
+    if (!std::isfinite(p->q_flux) || !std::isfinite(p->T0)) return fail(LBM_ERR_ARG, "non-finite q_flux / T0");
+    c->prm = *p;
+    c->have_params = true;
+    c->fwd_done = c->adj_done = false;
+    c->drop_graphs();
+    return LBM_OK;
+}
+
+lbm_status lbm_set_objective(lbm_ctx* c, const lbm_objective* o) {
+    if (!c || !o) return fail(LBM_ERR_ARG, "null argument");
+    if (!std::isfinite(o->w_pin) || !std::isfinite(o->w_tmean)) return fail(LBM_ERR_ARG, "non-finite weights");
+    c->obj = *o;
+    c->adj_done = false;
+    c->drop_graphs();
+    return LBM_OK;
+}
+
+lbm_status lbm_forward(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if ((st = check_opts(o)) != LBM_OK) return st;
+    double t0 = now_ms();
+    if ((st = enter(c)) != LBM_OK) return st;
+    if (o->reset || !c->fwd_done) {
+        if ((st = init_forward(c)) != LBM_OK) return st;
+    }
+    c->fwd_done = false;
+    c->adj_done = false;
+    long long s1 = 0, s2 = 0;
+    double res = 0, I = 0;
+    lbm_status st1 = run_phase(c, PH_FLOW, o, &s1, &res, &I);
+    lbm_status st2 = LBM_OK;
+    if (st1 >= 0 && c->thermal) {
+        double r2 = 0, I2 = 0;
+        st2 = run_phase(c, PH_THERM, o, &s2, &r2, &I2);
+        res = std::max(res, r2);
+        I = I2;
+    }
+    lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
+    if (final >= 0) c->fwd_done = true;
+    if (rep) {
+        rep->steps = s1 + s2;
+        rep->residual = res;
+        rep->I = I;
+        rep->J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        rep->ms = now_ms() - t0;
+        rep->status = final;
+    }
+    lbm_status lv = leave(c);
+    return final != LBM_OK ? final : lv;
+}
+
+lbm_status lbm_adjoint(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if ((st = check_opts(o)) != LBM_OK) return st;
+    if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_adjoint needs a completed lbm_forward");
+    double t0 = now_ms();
+    if ((st = enter(c)) != LBM_OK) return st;
+    if (o->reset || !c->adj_done) {
+        if ((st = init_adjoint(c)) != LBM_OK) return st;
+    }
+    c->adj_done = false;
+    long long s1 = 0, s2 = 0;
+    double res = 0, I = 0;
+    lbm_status st1 = LBM_OK, st2 = LBM_OK;
+    if (c->thermal) {
+        st1 = run_phase(c, PH_TADJ, o, &s1, &res, &I);
+        if (st1 >= 0) {
+            ThermLaunch t = therm_base(c);
+            t.gin = c->g[c->gcur];
+            t.ain = c->ga[c->gacur];
+            t.out0 = c->cpl;
+            t.out1 = c->sT;
+            cudaError_t e = thermal_launch(c->storage, TOP_COUPLING, t, c->geom, c->stream);
+            if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    if (st1 >= 0) {
+        double r2 = 0, I2 = 0;
+        st2 = run_phase(c, PH_ADJ, o, &s2, &r2, &I2);
+        res = std::max(res, r2);
+        I = I2;
+    }
+    lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
+    if (final >= 0) c->adj_done = true;
+    if (rep) {
+        rep->steps = s1 + s2;
+        rep->residual = res;
+        rep->I = I;
+        rep->J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        rep->ms = now_ms() - t0;
+        rep->status = final;
+    }
+    lbm_status lv = leave(c);
+    return final != LBM_OK ? final : lv;
+}
+
+lbm_status lbm_sensitivity(lbm_ctx* c, void* out, int dtype, int on_device) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "null argument");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    if (!c->adj_done) return fail(LBM_ERR_ORDER, "lbm_sensitivity needs a completed lbm_adjoint");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    FlowLaunch a = flow_base(c);
+    a.ain = c->fa[c->facur];
+    a.out0 = c->sens;
+    CUDA_TRY(flow_launch(c->stencil, c->storage, c->thermal ? FOP_SENS_T : FOP_SENS, a, c->geom, c->stream));
+    st = copy_out(c, out, c->sens, 1, dtype, on_device);
+    if (st != LBM_OK) return st;
+    return leave(c);
+}
+
+lbm_status lbm_get_fields(lbm_ctx* c, void* rho, void* u, void* T, int dtype, int on_device) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_get_fields needs a completed lbm_forward");
+    if (T && !c->thermal) return fail(LBM_ERR_ARG, "T requested without the thermal lattice");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    if (rho && (st = copy_out(c, rho, c->rho, 1, dtype, on_device)) != LBM_OK) return st;
+    if (u && (st = copy_out(c, u, c->u, 3, dtype, on_device)) != LBM_OK) return st;
+    if (T && (st = copy_out(c, T, c->T, 1, dtype, on_device)) != LBM_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return leave(c);
+}
+
+lbm_status lbm_get_objective(lbm_ctx* c, double* J) {
+    if (!c || !J) return fail(LBM_ERR_ARG, "null argument");
+    if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_get_objective needs a completed lbm_forward");
+    *J = c->J_p + (c->thermal ? c->J_T : 0.0);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_adjoint(lbm_ctx* c, void* fstar, void* gstar, int dtype, int on_device) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    if (!c->adj_done) return fail(LBM_ERR_ORDER, "lbm_get_adjoint needs a completed lbm_adjoint");
+    if (gstar && !c->thermal) return fail(LBM_ERR_ARG, "gstar requested without the thermal lattice");
+    if (c->ab != c->rb) return fail(LBM_ERR_UNSUPPORTED, "adjoint read-back for this storage");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    if (fstar && (st = copy_out(c, fstar, c->fa[c->facur], c->Q, dtype, on_device)) != LBM_OK) return st;
+    if (gstar && (st = copy_out(c, gstar, c->ga[c->gacur], 7, dtype, on_device)) != LBM_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return leave(c);
+}
+
+lbm_status lbm_time_steps(lbm_ctx* c, int phase, int n, double* ms_per_step) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if (!ms_per_step || n <= 0 || phase < 0 || phase > 3) return fail(LBM_ERR_ARG, "bad argument");
+    if ((phase == PH_THERM || phase == PH_TADJ) && !c->thermal)
+        return fail(LBM_ERR_ARG, "temperature phase without the thermal lattice");
+    if (phase != PH_FLOW && !c->fwd_done) return fail(LBM_ERR_ORDER, "needs a completed lbm_forward");
+    if ((st = enter(c)) != LBM_OK) return st;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, c->stream));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_step(c, phase, false, c->stream);
+    CUDA_TRY(e);
+    CUDA_TRY(cudaEventRecord(e1, c->stream));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_step = (double)ms / n;
+    return leave(c);
+}
+
+}  // extern "C"

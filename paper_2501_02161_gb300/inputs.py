@@ -288,3 +288,61 @@ def config_lattices(which: int, **kw):
         kw.setdefault("nz", 24)
         return heat_sink(**kw)
     raise ValueError(which)
+
+
+def six_port_box(nx: int = 14, ny: int = 12, nz: int = 10, width: int = 3,
+                 umax: float = 0.03, tau: float = 0.8, seed: int = 9,
+                 swap: bool = False, thermal: bool = False) -> Lattice:
+    """A walled box with one square opening centred on each of its six faces.
+
+    Without swap the openings on the low faces (normals +x, +y, +z) are
+    velocity inlets and those on the high faces (-x, -y, -z) fixed-density
+    outlets; swap exchanges the roles, so the two variants together cover both
+    boundary kinds in all six orientations.  gamma is seeded U[0.3, 1).
+    """
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    bc = np.zeros((nz, ny, nx, 4))
+    flags[0] = flags[-1] = WALL
+    flags[:, 0] = flags[:, -1] = WALL
+    flags[:, :, 0] = flags[:, :, -1] = WALL
+    dims = (nx, ny, nz)
+    for ax in range(3):
+        for side in (0, 1):
+            normal = [0, 0, 0]
+            normal[ax] = 1 if side == 0 else -1
+            inlet = (side == 0) != swap
+            kind = VEL if inlet else PRES
+            others = [a for a in range(3) if a != ax]
+            c0 = [dims[a] // 2 - width // 2 for a in others]
+            for i in range(width):
+                for j in range(width):
+                    pos = [0, 0, 0]
+                    pos[ax] = 0 if side == 0 else dims[ax] - 1
+                    pos[others[0]] = c0[0] + i
+                    pos[others[1]] = c0[1] + j
+                    x, y, z = pos
+                    flags[z, y, x] = make_flag(kind, tuple(normal))
+                    if inlet:
+                        prof = umax * parabola(i, width) * parabola(j, width)
+                        v = [0.0, 0.0, 0.0]
+                        v[ax] = prof * normal[ax]
+                        bc[z, y, x, :] = (*v, 0.1 * (ax + 1))
+                    else:
+                        bc[z, y, x, :] = (1.0 - 0.002 * ax, 0.0, 0.0, 0.0)
+    rng = np.random.default_rng(seed)
+    gam = 0.3 + 0.7 * rng.random((nz, ny, nx))
+    kind = flags & 7
+    gam[kind == WALL] = 0.0
+    lat = Lattice(f"six_port_{'b' if swap else 'a'}", D3Q19, nx, ny, nz, flags.ravel(),
+                  gam.ravel(), bc.ravel(), tau=tau)
+    if thermal:
+        lat.thermal = True
+        lat.kappa_f = 0.02
+        lat.k_ratio = 4.0
+        lat.w_tmean = 1.0
+        f3 = lat.flags.reshape(nz, ny, nx)
+        f3[0, 1:ny - 1, 1:nx - 1] = np.where((f3[0, 1:ny - 1, 1:nx - 1] & 7) == WALL,
+                                             make_flag(WALL, (0, 0, 1), heat=True),
+                                             f3[0, 1:ny - 1, 1:nx - 1])
+        lat.q_flux = 5e-3
+    return lat
