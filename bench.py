@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--roof-launches", type=int, default=20)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cap", type=int, default=CAP,
+                   help="step cap per solve phase (lower it only for profiler launch lists)")
     p.add_argument("--mode", default="full", choices=["full", "kernels"],
                    help="kernels: only time the fused step kernels on a --roof-n lattice")
     return p.parse_args()
@@ -180,8 +182,8 @@ def run_ours(args):
     def one_step():
         ups, launches, per = 0, 0, {}
         for re, s in solvers.items():
-            rf = s.forward(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
-            ra = (s.adjoint(tol=TOL, max_steps=CAP, check_every=CHECK, reset=True, strict=False)
+            rf = s.forward(tol=TOL, max_steps=args.cap, check_every=CHECK, reset=True, strict=False)
+            ra = (s.adjoint(tol=TOL, max_steps=args.cap, check_every=CHECK, reset=True, strict=False)
                   if rf.status >= 0 else rf.__class__(0, float("nan"), 0.0, 0.0, 0.0, rf.status))
             if ra.status >= 0:
                 s.sensitivity(out=sens)
