@@ -184,6 +184,50 @@ lbm_status lbm_get_adjoint(lbm_ctx* ctx, void* fstar, void* gstar, int dtype, in
  * (LBM_ERR_ORDER) and, for phases 1-3, a completed lbm_forward. */
 lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free single step (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * framework that owns every device allocation (a custom allocator or a memory
+ * pool it must not bypass), or code that runs where cudaMalloc is forbidden.
+ * The call runs one fused forward step with the residual / objective
+ * reduction on caller-owned buffers and allocates nothing: its reduction
+ * scratch is a static device array inside the library (512 KiB per GPU that
+ * loads the library, held until the process exits).
+ *
+ * Populations are the offset populations h_i = f_i - w_i rho0, population-
+ * major with `stride` elements between planes (stride >= nx*ny*nz); the rest
+ * state is h = 0.  gamma, bc, rho and u are double for LBM_FP64 storage and
+ * float otherwise; u has 3 planes of `stride`.  sums receives two doubles:
+ * the sum of |u| over non-wall nodes and the sum of rho over VEL nodes, both
+ * of the post-boundary state (the quantities the solver's residual and
+ * objective use).  All pointers are device pointers.
+ *
+ * The lattice may need at most 32768 reduction blocks (about 8.3 million
+ * nodes of 256-node tiles); larger lattices give LBM_ERR_ARG.  The first call
+ * on a device looks up the scratch array's device address, so make that first
+ * call before any stream capture.  Every call shares the one scratch array, so
+ * calls that overlap on the GPU (different streams, no ordering) race.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    int stencil;         /* lbm_stencil */
+    int storage;         /* lbm_storage (D2Q9: FP64 or FP32) */
+    int nx, ny, nz;
+    long long stride;    /* elements between population planes, >= nx*ny*nz */
+    const void* f_in;    /* Q planes, read */
+    void* f_out;         /* Q planes, written (must not alias f_in) */
+    const uint8_t* flags;
+    const void* gamma;
+    const void* bc;      /* 4 values per node, layout above */
+    void* rho;           /* out, nx*ny*nz values */
+    void* u;             /* out, 3 planes of stride */
+    double* sums;        /* out, 2 doubles */
+    double tau, rho0;
+    int gamma_model;
+} lbm_step_desc;
+
+lbm_status lbm_flow_step_noalloc(const lbm_step_desc* d, void* cuda_stream);
+
 /* Message for the last error on this thread (static storage, valid until the
  * next call on this thread). */
 const char* lbm_last_error(void);

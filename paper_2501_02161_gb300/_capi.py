@@ -46,6 +46,16 @@ class lbm_report(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class lbm_step_desc(ctypes.Structure):
+    _fields_ = [("stencil", ctypes.c_int), ("storage", ctypes.c_int), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("stride", ctypes.c_longlong),
+                ("f_in", ctypes.c_void_p), ("f_out", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("bc", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("sums", ctypes.c_void_p), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("gamma_model", ctypes.c_int)]
+
+
 # every entry point declared in include/lbmadj.h, with its ctypes signature
 _VP, _SZ, _I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
 SIGNATURES = {
@@ -64,6 +74,7 @@ SIGNATURES = {
     "lbm_get_objective": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "lbm_get_adjoint": (_I, [_VP, _VP, _VP, _I, _I]),
     "lbm_time_steps": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_flow_step_noalloc": (_I, [ctypes.POINTER(lbm_step_desc), _VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_version": (ctypes.c_char_p, []),
 }

@@ -82,6 +82,9 @@ cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, d
 cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64, long long n,
                            cudaStream_t s);
 
+// record an error message for lbm_last_error() and return the status
+int set_error(int status, const char* msg);
+
 // bytes per stored population / adjoint population / auxiliary value
 size_t pop_bytes(int storage);
 size_t adj_bytes(int storage);

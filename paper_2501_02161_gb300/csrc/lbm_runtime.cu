@@ -44,6 +44,11 @@ enum Phase { PH_FLOW = 0, PH_THERM = 1, PH_ADJ = 2, PH_TADJ = 3 };
 
 }  // namespace
 
+int lbm::set_error(int status, const char* msg) {
+    g_err = msg;
+    return status;
+}
+
 struct lbm_ctx {
     int device = 0;
     int stencil = 1, Q = 19, storage = 1;
