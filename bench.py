@@ -50,9 +50,85 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cap", type=int, default=CAP,
                    help="step cap per solve phase (lower it only for profiler launch lists)")
-    p.add_argument("--mode", default="full", choices=["full", "kernels"],
-                   help="kernels: only time the fused step kernels on a --roof-n lattice")
+    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd"],
+                   help="kernels: time the fused step kernels on a --roof-n lattice; "
+                        "precision: heat sink in FP64/FP32/FP16/BF16 storage, error per field; "
+                        "autograd: the filtered / projected gradient loop")
+    p.add_argument("--iters", type=int, default=50, help="autograd mode: optimisation iterations")
     return p.parse_args()
+
+
+def run_precision(args):
+    """128x64x32 heat sink (D3Q19 + D3Q7) solved to 1e-6 in each storage;
+    rel-L2 error of every field against the FP64 run (whose parity with the
+    FP64 oracle the tests establish) and the forward + adjoint MLUPS."""
+    import numpy as np
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    out = {"mode": "precision", "workload": "heat sink 128x64x32, Re 50, Pr 7, k_r 100, "
+                                            "forward + adjoint to 1e-6 (temperature lattice included)",
+           "fields": {}}
+    ref = None
+    for storage in ("fp64", "fp32", "fp16", "bf16"):
+        lat = I.heat_sink(re=50.0, seed=4)
+        s = Solver.from_lattice(lat, storage=storage, device="cuda:0")
+        t0 = time.perf_counter()
+        rf = s.forward(tol=TOL, max_steps=400000, check_every=CHECK, strict=False)
+        ra = s.adjoint(tol=TOL, max_steps=400000, check_every=CHECK, strict=False) if rf.status >= 0 else None
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rec = {"fwd_steps": rf.steps, "fwd_status": rf.status, "J": rf.J,
+               "adj_steps": ra.steps if ra else 0, "adj_status": ra.status if ra else None,
+               "MLUPS": round((rf.steps + (ra.steps if ra else 0)) * lat.n / dt / 1e6, 1)}
+        if ra is not None and ra.status >= 0:
+            rho, u, T = s.fields(torch.float64)
+            fs, gs = s.adjoint_fields(torch.float64)
+            f = {"rho": rho, "u": u, "T": T, "f*": fs, "g*": gs,
+                 "dJ/dgamma": s.sensitivity(dtype=torch.float64), "J": torch.tensor([rf.J])}
+            f = {k: v.cpu().numpy() for k, v in f.items()}
+            if storage == "fp64":
+                ref = f
+            else:
+                rec["rel_l2_vs_fp64"] = {k: float(np.linalg.norm(f[k] - ref[k]) / np.linalg.norm(ref[k]))
+                                         for k in f}
+        out["fields"][storage] = rec
+        s.close()
+    print(json.dumps(out))
+
+
+def run_autograd(args):
+    """The autograd workload: 96x48x24 heat sink, density filter (radius 2) +
+    Heaviside projection (beta 8), --iters projected-gradient steps, each a
+    forward + adjoint through the C-ABI with warm starts."""
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.autograd import SolveOpts, projected_gradient_loop
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    lat = I.heat_sink(nx=96, ny=48, nz=24, re=50.0, seed=4)
+    s = Solver.from_lattice(lat, storage=args.storage, device="cuda:0")
+    t0 = time.perf_counter()
+    rho, hist = projected_gradient_loop(s, lat, iters=args.iters, step=0.05, volume=0.6,
+                                        opts=SolveOpts(tol=1e-5, max_steps=200000,
+                                                       check_every=500, warm=True))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"mode": "autograd", "workload": "heat sink 96x48x24 Re 50, filter r=2, "
+                      "projection beta=8, volume fraction 0.6 penalty, tol 1e-5 warm-started",
+                      "iters": args.iters, "seconds": round(dt, 2),
+                      "s_per_iter": round(dt / args.iters, 3),
+                      "J": [round(h["J"], 6) for h in hist],
+                      "loss": [round(h["loss"], 6) for h in hist]}))
 
 
 def run_kernels(args):
@@ -431,5 +507,9 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.mode == "kernels":
         run_kernels(a)
+    elif a.mode == "precision":
+        run_precision(a)
+    elif a.mode == "autograd":
+        run_autograd(a)
     else:
         run_ours(a)

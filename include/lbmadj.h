@@ -72,8 +72,11 @@ typedef enum {
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_stencil;
 
-/* Population storage.  FP16/BF16 store f - w_i * rho0 (flow) and
- * g - w_k * T0 (temperature) and compute in FP32. */
+/* Population storage.  Flow populations are always held as offsets
+ * h_i = f_i - w_i rho0.  FP16_OFS / BF16_OFS store the flow populations h in
+ * 16 bits and compute in FP32; in those modes the adjoint and temperature
+ * populations stay FP32 (their slowly converging linear iterations would
+ * accumulate 16-bit rounding into percent-level errors). */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_OFS = 2, LBM_BF16_OFS = 3 } lbm_storage;
 
 typedef enum { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 } lbm_dtype;
@@ -103,7 +106,10 @@ typedef struct {
     double tol;          /* stop when |I(t)-I(t-K)|/|I(t)| < tol; tol <= 0: run exactly max_steps */
     long long max_steps; /* step cap (or exact count when tol <= 0); >= 0 */
     int check_every;     /* K, steps between residual checks (> 0; the paper uses 1000) */
-    int reset;           /* 1: restart from the initial state; 0: continue (warm start) */
+    int reset;           /* 1: restart from the initial state; 0: continue from the populations
+                            left by the previous solve of this phase (a warm start that stays
+                            valid across lbm_set_gamma / set_bc_values / set_params; lbm_set_flags
+                            and a diverged solve discard it) */
 } lbm_solve_opts;
 
 typedef struct {

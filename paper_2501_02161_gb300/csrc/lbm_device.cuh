@@ -305,19 +305,20 @@ __device__ __forceinline__ void zou_he_adjoint(R (&c)[L::Q], int type, int code)
         }
     }
     if (type != PRES) P = R(0);
-    R out[L::Q];
+    // in place: the unknowns are read (through opp) before they are zeroed
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
-        if (d > 0)
-            out[i] = R(0);
-        else if (d < 0)
-            out[i] = c[i] + c[L::opp(i)] - R(2) * P;
-        else
-            out[i] = c[i] - R(0.5) * (R(L::cx(i)) * M0 + R(L::cy(i)) * M1 + R(L::cz(i)) * M2) - P;
+        if (d < 0)
+            c[i] = c[i] + c[L::opp(i)] - R(2) * P;
+        else if (d == 0)
+            c[i] = c[i] - R(0.5) * (R(L::cx(i)) * M0 + R(L::cy(i)) * M1 + R(L::cz(i)) * M2) - P;
     }
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) c[i] = out[i];
+    for (int i = 0; i < L::Q; ++i) {
+        const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
+        if (d > 0) c[i] = R(0);
+    }
 }
 
 template <class L, typename R>
@@ -388,8 +389,8 @@ __global__ void __launch_bounds__(256) k_flow_step(FlowArgs<T, TA, R> a) {
         }
         if (type != WALL) {
             if (REDUCE) {
-                acc[0] = sqrt((double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2);
-                if (type == VEL) acc[1] = (double)a.rho0 + (double)drho;
+                acc[0] = (double)sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+                if (type == VEL) acc[1] = (double)(a.rho0 + drho);
             }
             const R g = a.gamma[c.n];
             R a0, a1, a2, amp;
@@ -467,8 +468,17 @@ __device__ __forceinline__ void pull_adjoint(const FlowArgs<T, TA, R>& a, const 
     }
 }
 
+// resident 256-thread blocks per SM requested from the compiler: the plain
+// FP32-math D3Q19 adjoint fits 40 registers without spilling (6 blocks, 75 %
+// occupancy); other variants keep the compiler's choice
+template <class L, typename R, bool HOT>
+struct AdjMinBlocks {
+    static constexpr int value = (L::Q == 19 && sizeof(R) == 4 && HOT) ? 6 : 1;
+};
+
 template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
-__global__ void __launch_bounds__(256) k_flow_adjoint(FlowArgs<T, TA, R> a) {
+__global__ void __launch_bounds__(256, (AdjMinBlocks<L, R, !REDUCE && !THERMAL>::value))
+    k_flow_adjoint(FlowArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
     if (c.active) {
@@ -513,10 +523,10 @@ __global__ void __launch_bounds__(256) k_flow_adjoint(FlowArgs<T, TA, R> a) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) Pop<TA>::st(a.aout, (size_t)i * a.np + c.n, s[i] * inv, R(0));
         if (REDUCE && type != WALL) {
-            double t = 0.0;
+            R t = 0;
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) t += fabs((double)s[i]);
-            acc[0] = t;
+            for (int i = 0; i < L::Q; ++i) t += fabs(s[i]);
+            acc[0] = (double)t;
         }
     }
     if (REDUCE) block_partials<1>(acc, a.partials);
@@ -735,10 +745,10 @@ __global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) 
 #pragma unroll
         for (int k = 0; k < 7; ++k) Pop<TA>::st(a.aout, (size_t)k * a.np + c.n, s[k] * inv, R(0));
         if (REDUCE && type != WALL) {
-            double t = 0.0;
+            R t = 0;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) t += fabs((double)s[k]);
-            acc[0] = t;
+            for (int k = 0; k < 7; ++k) t += fabs(s[k]);
+            acc[0] = (double)t;
         }
     }
     if (REDUCE) block_partials<1>(acc, a.partials);

@@ -85,9 +85,11 @@ cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64,
 // record an error message for lbm_last_error() and return the status
 int set_error(int status, const char* msg);
 
-// bytes per stored population / adjoint population / auxiliary value
+// bytes per stored flow population / adjoint population / auxiliary value /
+// temperature population
 size_t pop_bytes(int storage);
 size_t adj_bytes(int storage);
 size_t aux_bytes(int storage);
+size_t heat_bytes(int storage);
 
 }  // namespace lbm

@@ -22,10 +22,15 @@ namespace {
 template <typename T> struct Types;
 // storage -> (population type, adjoint type, compute type)
 template <int S> struct StorageTypes;
-template <> struct StorageTypes<0> { using T = double; using TA = double; using R = double; };
-template <> struct StorageTypes<1> { using T = float; using TA = float; using R = float; };
-template <> struct StorageTypes<2> { using T = __half; using TA = float; using R = float; };
-template <> struct StorageTypes<3> { using T = __nv_bfloat16; using TA = float; using R = float; };
+// T: flow populations, TG: temperature populations, TA: adjoint populations.
+// The 16-bit modes narrow only the flow populations: the adjoint and the
+// temperature lattice converge slowly (thousands of sweeps of a linear
+// iteration), and 11- or 8-bit mantissas accumulate into percent-level errors
+// there, so they stay FP32.
+template <> struct StorageTypes<0> { using T = double; using TG = double; using TA = double; using R = double; };
+template <> struct StorageTypes<1> { using T = float; using TG = float; using TA = float; using R = float; };
+template <> struct StorageTypes<2> { using T = __half; using TG = float; using TA = float; using R = float; };
+template <> struct StorageTypes<3> { using T = __nv_bfloat16; using TG = float; using TA = float; using R = float; };
 
 template <int S>
 FlowArgs<typename StorageTypes<S>::T, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
@@ -60,9 +65,9 @@ flow_args(const FlowLaunch& l) {
 }
 
 template <int S>
-ThermArgs<typename StorageTypes<S>::T, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
+ThermArgs<typename StorageTypes<S>::TG, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
 therm_args(const ThermLaunch& l) {
-    using T = typename StorageTypes<S>::T;
+    using T = typename StorageTypes<S>::TG;
     using TA = typename StorageTypes<S>::TA;
     using R = typename StorageTypes<S>::R;
     ThermArgs<T, TA, R> a;
@@ -117,7 +122,7 @@ void flow_dispatch(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t s
 
 template <int S>
 void therm_dispatch(ThermOp op, const ThermLaunch& l, const Geom& g, cudaStream_t s) {
-    using T = typename StorageTypes<S>::T;
+    using T = typename StorageTypes<S>::TG;
     using TA = typename StorageTypes<S>::TA;
     using R = typename StorageTypes<S>::R;
     auto a = therm_args<S>(l);
@@ -198,6 +203,7 @@ cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64,
 
 size_t pop_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 size_t adj_bytes(int storage) { return storage == 0 ? 8 : 4; }
+size_t heat_bytes(int storage) { return storage == 0 ? 8 : 4; }
 size_t aux_bytes(int storage) { return storage == 0 ? 8 : 4; }
 
 }  // namespace lbm

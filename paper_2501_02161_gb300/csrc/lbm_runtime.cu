@@ -88,6 +88,7 @@ struct lbm_ctx {
     long long n_in = 0, n_nw = 0;
     bool have_flags = false, have_gamma = false, have_bc = false, have_params = false;
     bool fwd_done = false, adj_done = false;
+    bool fstate = false, astate = false;  // populations hold a usable (warm-start) state
     double J_p = 0.0, J_T = 0.0;
     double last_I[4] = {0, 0, 0, 0};
 
@@ -469,7 +470,7 @@ lbm_status lbm_create(lbm_ctx** out, int stencil, int nx, int ny, int nz, int st
         c->f[b] = dalloc(np * c->Q * c->pb, &e);
         c->fa[b] = dalloc(np * c->Q * c->ab, &e);
         if (c->thermal) {
-            c->g[b] = dalloc(np * 7 * c->pb, &e);
+            c->g[b] = dalloc(np * 7 * heat_bytes(storage), &e);
             c->ga[b] = dalloc(np * 7 * c->ab, &e);
         }
     }
@@ -546,6 +547,7 @@ lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_devi
     c->n_nw = nnw;
     c->have_flags = true;
     c->fwd_done = c->adj_done = false;
+    c->fstate = c->astate = false;
     c->drop_graphs();  // objective source depends on N_in / N_nonwall
     return leave(c);
 }
@@ -607,8 +609,9 @@ lbm_status lbm_forward(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     if ((st = check_opts(o)) != LBM_OK) return st;
     double t0 = now_ms();
     if ((st = enter(c)) != LBM_OK) return st;
-    if (o->reset || !c->fwd_done) {
+    if (o->reset || !c->fstate) {
         if ((st = init_forward(c)) != LBM_OK) return st;
+        c->fstate = true;
     }
     c->fwd_done = false;
     c->adj_done = false;
@@ -624,6 +627,7 @@ lbm_status lbm_forward(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     }
     lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
     if (final >= 0) c->fwd_done = true;
+    else c->fstate = false;
     if (rep) {
         rep->steps = s1 + s2;
         rep->residual = res;
@@ -643,8 +647,9 @@ lbm_status lbm_adjoint(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_adjoint needs a completed lbm_forward");
     double t0 = now_ms();
     if ((st = enter(c)) != LBM_OK) return st;
-    if (o->reset || !c->adj_done) {
+    if (o->reset || !c->astate) {
         if ((st = init_adjoint(c)) != LBM_OK) return st;
+        c->astate = true;
     }
     c->adj_done = false;
     long long s1 = 0, s2 = 0;
@@ -670,6 +675,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     }
     lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
     if (final >= 0) c->adj_done = true;
+    else c->astate = false;
     if (rep) {
         rep->steps = s1 + s2;
         rep->residual = res;
@@ -723,7 +729,6 @@ lbm_status lbm_get_adjoint(lbm_ctx* c, void* fstar, void* gstar, int dtype, int 
     if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
     if (!c->adj_done) return fail(LBM_ERR_ORDER, "lbm_get_adjoint needs a completed lbm_adjoint");
     if (gstar && !c->thermal) return fail(LBM_ERR_ARG, "gstar requested without the thermal lattice");
-    if (c->ab != c->rb) return fail(LBM_ERR_UNSUPPORTED, "adjoint read-back for this storage");
     lbm_status st = enter(c);
     if (st != LBM_OK) return st;
     if (fstar && (st = copy_out(c, fstar, c->fa[c->facur], c->Q, dtype, on_device)) != LBM_OK) return st;

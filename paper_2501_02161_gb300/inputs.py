@@ -114,19 +114,23 @@ def gaussian_filter_nearest(a: np.ndarray, sigma: float) -> np.ndarray:
 
 
 def filtered_design(shape_zyx, seed: int, sigma: float = 3.0,
-                    mean: float = 0.5, std: float = 0.25) -> np.ndarray:
-    """Gaussian-filtered uniform noise, affinely rescaled, clipped to [0,1].
+                    fluid_fraction: float = 0.75, sharpness: float = 3.0) -> np.ndarray:
+    """A near-binary random design in [0,1] from Gaussian-filtered uniform noise.
 
-    Filtered U[0,1) noise has a standard deviation of about 0.01 at sigma=3,
-    so clipping alone would leave a near-uniform 0.5 field; the rescale to
-    (mean, std) keeps the spatial structure and gives solid-like and fluid-like
-    regions.
+    Filtered U[0,1) noise has a standard deviation of only about 0.01 at
+    sigma=3, so clipping it leaves gamma ~ 0.5 everywhere: a uniform, very
+    strong Brinkman drag that no topology-optimisation design has.  The field
+    is therefore standardised and passed through a smooth step
+    gamma = (1 + tanh(sharpness (z - z_q))) / 2 placed at the quantile z_q that
+    leaves `fluid_fraction` of the nodes fluid-like, which keeps the noise's
+    spatial structure (blobs of about sigma cells) and the [0,1] range.
     """
     n = int(np.prod(shape_zyx))
     g = gaussian_filter_nearest(uniform_noise(n, seed).reshape(shape_zyx), sigma)
     s = g.std()
-    g = (g - g.mean()) / (s if s > 0 else 1.0) * std + mean
-    return np.clip(g, 0.0, 1.0)
+    z = (g - g.mean()) / (s if s > 0 else 1.0)
+    zq = np.quantile(z, 1.0 - fluid_fraction)
+    return np.clip(0.5 * (1.0 + np.tanh(sharpness * (z - zq))), 0.0, 1.0)
 
 
 # --------------------------------------------------------------------------
@@ -227,7 +231,7 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
               re: float = 50.0, pr: float = 7.0, k_ratio: float = 100.0,
               q_flux: float = 1e-3, seed: int = 4, sigma: float = 3.0,
               w_pin: float = 1.0, w_tmean: float = 1.0,
-              gamma_uniform: float | None = None,
+              gamma_uniform: float | None = None, plenum: int = 4,
               gamma_model: int = GAMMA_EQ12) -> Lattice:
     """Microchannel heat sink (Fig. 15), flow along +x through a design block.
 
@@ -235,6 +239,7 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
     (velocity inlet with a product parabola and T=0; fixed-density outlet).
     Walls on y=0, y=ny-1, z=0, z=nz-1; the z=0 wall under the interior is
     heated with q_flux per node and step.  Re uses the smaller inlet side.
+    The first and last `plenum` x-layers are fluid (gamma = 1).
     """
     flags = np.zeros((nz, ny, nx), np.uint8)
     bc = np.zeros((nz, ny, nx, 4))
@@ -254,6 +259,9 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
         gam = np.full((nz, ny, nx), float(gamma_uniform))
     else:
         gam = filtered_design((nz, ny, nx), seed, sigma)
+        # inlet and outlet plenums outside the design block (Fig. 15)
+        gam[:, :, :plenum] = 1.0
+        gam[:, :, nx - plenum:] = 1.0
     kind = flags & 7
     gam[(kind == VEL) | (kind == PRES)] = 1.0
     gam[kind == WALL] = 0.0
