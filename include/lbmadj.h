@@ -191,6 +191,53 @@ lbm_status lbm_get_adjoint(lbm_ctx* ctx, void* fstar, void* gstar, int dtype, in
 lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
 
 /* ---------------------------------------------------------------------------
+ * Batched solves (serving)
+ *
+ * A batch advances many resident contexts together: every call of
+ * lbm_batch_step runs check_every steps of each admitted context's current
+ * phase (flow, temperature, temperature adjoint, flow adjoint) as one CUDA
+ * graph replay of persistent kernels that walk the tiles of all resident
+ * lattices, then checks each context's residual exactly as lbm_forward /
+ * lbm_adjoint do (same step counts, same FP64 sums), so a context's results
+ * are bit-identical alone, in any mix, and through the single-context calls.
+ * Contexts may be admitted and retired between steps (continuous batching);
+ * admission never re-captures the graph.  Built for D3Q19 with FP32, FP16_OFS
+ * or BF16_OFS storage.
+ * --------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Bytes of device memory lbm_create allocates for a context of this shape
+ * (for admission by HBM footprint). */
+size_t lbm_footprint_bytes(int stencil, int nx, int ny, int nz, int storage, int thermal);
+
+/* storage: the storage every admitted context must use; check_every: K, even,
+ * the residual-check interval (and graph length); max_slots: resident contexts
+ * at most.  Errors: LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (FP64), LBM_ERR_OOM. */
+lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots);
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Queue a context (inputs set, D3Q19, the batch's storage) for a forward +
+ * adjoint solve with opts->tol and opts->max_steps per phase (opts->check_every
+ * is ignored: the batch's K applies; opts->reset = 0 warm-starts from the
+ * context's previous populations).  The context must not be used by other
+ * calls until it is returned by lbm_batch_poll.  *slot receives its slot id.
+ * Errors: LBM_ERR_ARG (wrong storage/stencil, batch full), LBM_ERR_ORDER
+ * (inputs missing). */
+lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* ctx, const lbm_solve_opts* opts, int* slot);
+
+/* Advance every admitted context by K steps of its current phase and move
+ * contexts whose phase converged (or hit its cap, or diverged) on; *n_active
+ * receives the contexts still running.  Synchronises. */
+lbm_status lbm_batch_step(lbm_batch* b, int* n_active);
+
+/* Contexts that finished since the last poll: up to max (slot, context,
+ * report) triples; *n receives the count.  A finished context is released
+ * from the batch; lbm_sensitivity / lbm_get_fields on it work as after
+ * lbm_adjoint (report->status < 0: the solve failed, e.g. diverged). */
+lbm_status lbm_batch_poll(lbm_batch* b, int* slots, lbm_ctx** ctxs, lbm_report* reports, int max,
+                          int* n);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free single step (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory: code running inside a

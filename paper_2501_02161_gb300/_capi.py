@@ -75,6 +75,13 @@ SIGNATURES = {
     "lbm_get_adjoint": (_I, [_VP, _VP, _VP, _I, _I]),
     "lbm_time_steps": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "lbm_flow_step_noalloc": (_I, [ctypes.POINTER(lbm_step_desc), _VP]),
+    "lbm_footprint_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I, _I]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I]),
+    "lbm_batch_destroy": (None, [_VP]),
+    "lbm_batch_admit": (_I, [_VP, _VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(_I)]),
+    "lbm_batch_step": (_I, [_VP, ctypes.POINTER(_I)]),
+    "lbm_batch_poll": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(lbm_report),
+                            _I, ctypes.POINTER(_I)]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_version": (ctypes.c_char_p, []),
 }

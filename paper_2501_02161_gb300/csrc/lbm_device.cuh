@@ -203,8 +203,15 @@ __device__ __forceinline__ long long shifted(const Cell& c, int i, int s, int nx
     return x + (long long)nx * (y + (long long)ny * z);
 }
 
+__device__ __forceinline__ long long grid_block_id() {
+    return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
+// per-block FP64 partial sums of NV values (warp shuffles + shared memory),
+// written to partials[b*NV + k]; ends with a barrier so the block may reuse
+// the shared scratch for another tile
 template <int NV>
-__device__ __forceinline__ void block_partials(double (&v)[NV], double* __restrict__ partials) {
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* __restrict__ partials, long long b) {
     __shared__ double sh[NV][32];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int lane = tid & 31, warp = tid >> 5;
@@ -217,7 +224,6 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* __restri
     }
     __syncthreads();
     if (warp == 0) {
-        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double s = lane < nwarps ? sh[k][lane] : 0.0;
@@ -225,6 +231,7 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* __restri
             if (lane == 0) partials[b * NV + k] = s;
         }
     }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -372,47 +379,50 @@ __device__ __forceinline__ void moments(const R (&f)[L::Q], R rho0, R& rho, R& u
 // forward kernels
 // ---------------------------------------------------------------------------
 template <class L, typename T, typename TA, typename R, bool REDUCE>
+__device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
+    R f[L::Q];
+    const int fl = pull_forward<L>(a, c, f);
+    const int type = fl & 7;
+    R drho, u0, u1, u2;
+    moments<L>(f, a.rho0, drho, u0, u1, u2);
+    if (REDUCE) {  // the fields and the frozen velocity of this post-boundary state
+        a.out0[c.n] = a.rho0 + drho;
+        a.out1[c.n] = u0;
+        a.out1[a.np + c.n] = u1;
+        a.out1[2 * a.np + c.n] = u2;
+    }
+    if (type != WALL) {
+        if (REDUCE) {
+            acc[0] = (double)sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+            if (type == VEL) acc[1] = (double)(a.rho0 + drho);
+        }
+        const R g = a.gamma[c.n];
+        R a0, a1, a2, amp;
+        if (a.model == 0) {
+            a0 = g * u0; a1 = g * u1; a2 = g * u2; amp = R(1);
+        } else {
+            a0 = u0; a1 = u1; a2 = u2; amp = g;
+        }
+        const R uu = a0 * a0 + a1 * a1 + a2 * a2;
+        const R om = a.omega;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const R eu = R(L::cx(i)) * a0 + R(L::cy(i)) * a1 + R(L::cz(i)) * a2;
+            const R heq = R(L::w(i)) * (drho + a.rho0 * amp * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
+            f[i] += om * (heq - f[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        Pop<T>::st(a.fout, (size_t)i * a.np + c.n, f[i], R(0));
+}
+
+template <class L, typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_flow_step(FlowArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     double acc[2] = {0.0, 0.0};
-    if (c.active) {
-        R f[L::Q];
-        const int fl = pull_forward<L>(a, c, f);
-        const int type = fl & 7;
-        R drho, u0, u1, u2;
-        moments<L>(f, a.rho0, drho, u0, u1, u2);
-        if (REDUCE) {  // the fields and the frozen velocity of this post-boundary state
-            a.out0[c.n] = a.rho0 + drho;
-            a.out1[c.n] = u0;
-            a.out1[a.np + c.n] = u1;
-            a.out1[2 * a.np + c.n] = u2;
-        }
-        if (type != WALL) {
-            if (REDUCE) {
-                acc[0] = (double)sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-                if (type == VEL) acc[1] = (double)(a.rho0 + drho);
-            }
-            const R g = a.gamma[c.n];
-            R a0, a1, a2, amp;
-            if (a.model == 0) {
-                a0 = g * u0; a1 = g * u1; a2 = g * u2; amp = R(1);
-            } else {
-                a0 = u0; a1 = u1; a2 = u2; amp = g;
-            }
-            const R uu = a0 * a0 + a1 * a1 + a2 * a2;
-            const R om = a.omega;
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) {
-                const R eu = R(L::cx(i)) * a0 + R(L::cy(i)) * a1 + R(L::cz(i)) * a2;
-                const R heq = R(L::w(i)) * (drho + a.rho0 * amp * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
-                f[i] += om * (heq - f[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i)
-            Pop<T>::st(a.fout, (size_t)i * a.np + c.n, f[i], R(0));
-    }
-    if (REDUCE) block_partials<2>(acc, a.partials);
+    if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
+    if (REDUCE) block_partials<2>(acc, a.partials, grid_block_id());
 }
 
 // f = f^eq(rho0, 0) = w rho0, i.e. h = 0 (collision leaves it unchanged); f* = 0
@@ -477,59 +487,62 @@ struct AdjMinBlocks {
 };
 
 template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
+__device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
+    R s[L::Q];
+    pull_adjoint<L>(a, c, s);
+    const int fl = a.flags[c.n];
+    const int type = fl & 7;
+    if (type == WALL) {
+        bounce<L>(s);  // C^T = I, B^T = the same swap
+    } else {
+        const R g = a.gamma[c.n];
+        const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+        AdjMoments<L, R> m;
+        m.compute(s);
+        const R Qu0 = m.Q00 * u0 + m.Q01 * u1 + m.Q02 * u2;
+        const R Qu1 = m.Q01 * u0 + m.Q11 * u1 + m.Q12 * u2;
+        const R Qu2 = m.Q02 * u0 + m.Q12 * u1 + m.Q22 * u2;
+        // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
+        const R c1 = R(3) * g;
+        const R c2 = a.model == 0 ? R(9) * g * g : R(9) * g;
+        const R c3 = a.model == 0 ? R(3) * g * g : R(3) * g;
+        R w0 = c1 * m.M0 + c2 * Qu0 - c3 * m.A * u0;
+        R w1 = c1 * m.M1 + c2 * Qu1 - c3 * m.A * u1;
+        R w2 = c1 * m.M2 + c2 * Qu2 - c3 * m.A * u2;
+        const R om = a.omega;
+        const R base = om * m.A - (type == VEL ? a.src_in : R(0));
+        R v0 = 0, v1 = 0, v2 = 0;
+        if (THERMAL) {
+            v0 = a.cpl[c.n];
+            v1 = a.cpl[a.np + c.n];
+            v2 = a.cpl[2 * a.np + c.n];
+        }
+        w0 = om * w0 + v0;
+        w1 = om * w1 + v1;
+        w2 = om * w2 + v2;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            s[i] = (R(1) - om) * s[i] + base + R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
+        if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
+    }
+    const R inv = R(1) / a.ascale;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Pop<TA>::st(a.aout, (size_t)i * a.np + c.n, s[i] * inv, R(0));
+    if (REDUCE && type != WALL) {
+        R t = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) t += fabs(s[i]);
+        acc[0] = (double)t;
+    }
+}
+
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
 __global__ void __launch_bounds__(256, (AdjMinBlocks<L, R, !REDUCE && !THERMAL>::value))
     k_flow_adjoint(FlowArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
-    if (c.active) {
-        R s[L::Q];
-        pull_adjoint<L>(a, c, s);
-        const int fl = a.flags[c.n];
-        const int type = fl & 7;
-        if (type == WALL) {
-            bounce<L>(s);  // C^T = I, B^T = the same swap
-        } else {
-            const R g = a.gamma[c.n];
-            const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
-            AdjMoments<L, R> m;
-            m.compute(s);
-            const R Qu0 = m.Q00 * u0 + m.Q01 * u1 + m.Q02 * u2;
-            const R Qu1 = m.Q01 * u0 + m.Q11 * u1 + m.Q12 * u2;
-            const R Qu2 = m.Q02 * u0 + m.Q12 * u1 + m.Q22 * u2;
-            // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
-            const R c1 = R(3) * g;
-            const R c2 = a.model == 0 ? R(9) * g * g : R(9) * g;
-            const R c3 = a.model == 0 ? R(3) * g * g : R(3) * g;
-            R w0 = c1 * m.M0 + c2 * Qu0 - c3 * m.A * u0;
-            R w1 = c1 * m.M1 + c2 * Qu1 - c3 * m.A * u1;
-            R w2 = c1 * m.M2 + c2 * Qu2 - c3 * m.A * u2;
-            const R om = a.omega;
-            const R base = om * m.A - (type == VEL ? a.src_in : R(0));
-            R v0 = 0, v1 = 0, v2 = 0;
-            if (THERMAL) {
-                v0 = a.cpl[c.n];
-                v1 = a.cpl[a.np + c.n];
-                v2 = a.cpl[2 * a.np + c.n];
-            }
-            w0 = om * w0 + v0;
-            w1 = om * w1 + v1;
-            w2 = om * w2 + v2;
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i)
-                s[i] = (R(1) - om) * s[i] + base + R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
-            if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
-        }
-        const R inv = R(1) / a.ascale;
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) Pop<TA>::st(a.aout, (size_t)i * a.np + c.n, s[i] * inv, R(0));
-        if (REDUCE && type != WALL) {
-            R t = 0;
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) t += fabs(s[i]);
-            acc[0] = (double)t;
-        }
-    }
-    if (REDUCE) block_partials<1>(acc, a.partials);
+    if (c.active) flow_adjoint_node<L, T, TA, R, REDUCE, THERMAL>(a, c, acc);
+    if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
 }
 
 // J'(x) = -(1/tau) sum_i f*_S,i d f^eq_i / d gamma (Eq. 66), + thermal part
@@ -631,35 +644,38 @@ __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const 
 }
 
 template <typename T, typename TA, typename R, bool REDUCE>
+__device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
+    R g[7], gam, u0, u1, u2;
+    const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
+    R tem = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) tem += g[k];
+    if (REDUCE) {  // temperature and frozen post-boundary g of this state
+        a.out0[c.n] = tem;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + c.n] = g[k];
+    }
+    if ((fl & 7) != WALL) {
+        if (REDUCE) acc[0] = (double)tem;
+        const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
+        const R g4 = R(4) * gam;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const R geq = R(D3Q7::w(k)) * tem * (R(1) + g4 * ecomp<R>(k, u0, u1, u2));
+            g[k] += om * (geq - g[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);
+}
+
+template <typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_thermal_step(ThermArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
-    if (c.active) {
-        R g[7], gam, u0, u1, u2;
-        const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
-        R tem = 0;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) tem += g[k];
-        if (REDUCE) {  // temperature and frozen post-boundary g of this state
-            a.out0[c.n] = tem;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + c.n] = g[k];
-        }
-        if ((fl & 7) != WALL) {
-            if (REDUCE) acc[0] = (double)tem;
-            const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
-            const R g4 = R(4) * gam;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                const R geq = R(D3Q7::w(k)) * tem * (R(1) + g4 * ecomp<R>(k, u0, u1, u2));
-                g[k] += om * (geq - g[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 7; ++k)
-            Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);
-    }
-    if (REDUCE) block_partials<1>(acc, a.partials);
+    if (c.active) thermal_step_node<T, TA, R, REDUCE>(a, c, acc);
+    if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
 }
 
 template <typename T, typename TA, typename R>
@@ -705,53 +721,56 @@ __device__ __forceinline__ void thermal_pull_adjoint(const ThermArgs<T, TA, R>& 
 }
 
 template <typename T, typename TA, typename R, bool REDUCE>
+__device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
+    R s[7];
+    thermal_pull_adjoint(a, c, s);
+    const int fl = a.flags[c.n];
+    const int type = fl & 7;
+    if (type == WALL) {
+        bounce<D3Q7>(s);
+    } else {
+        const R gam = a.gamma[c.n];
+        const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+        const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
+        thermal_adjoint_collide<R>(s, gam, u0, u1, u2, om, a.src_T);
+        if (type >= VEL) {
+            const int kn = ((fl >> 3) & 7) + 1;
+            R ckn = 0, en = 0;
+#pragma unroll
+            for (int k = 1; k < 7; ++k)
+                if (k == kn) {
+                    ckn = s[k];
+                    en = ecomp<R>(k, u0, u1, u2);
+                }
+            R coef;
+            if (type == VEL) {
+                coef = R(-1);
+            } else {
+                const R wa = R(0.125) * (R(1) + R(4) * gam * en);
+                coef = wa / (R(1) - wa);
+                a.gcn[c.n] = ckn;
+            }
+#pragma unroll
+            for (int k = 0; k < 7; ++k) s[k] = (k == kn) ? R(0) : s[k] + coef * ckn;
+        }
+    }
+    const R inv = R(1) / a.ascale;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) Pop<TA>::st(a.aout, (size_t)k * a.np + c.n, s[k] * inv, R(0));
+    if (REDUCE && type != WALL) {
+        R t = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) t += fabs(s[k]);
+        acc[0] = (double)t;
+    }
+}
+
+template <typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
-    if (c.active) {
-        R s[7];
-        thermal_pull_adjoint(a, c, s);
-        const int fl = a.flags[c.n];
-        const int type = fl & 7;
-        if (type == WALL) {
-            bounce<D3Q7>(s);
-        } else {
-            const R gam = a.gamma[c.n];
-            const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
-            const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
-            thermal_adjoint_collide<R>(s, gam, u0, u1, u2, om, a.src_T);
-            if (type >= VEL) {
-                const int kn = ((fl >> 3) & 7) + 1;
-                R ckn = 0, en = 0;
-#pragma unroll
-                for (int k = 1; k < 7; ++k)
-                    if (k == kn) {
-                        ckn = s[k];
-                        en = ecomp<R>(k, u0, u1, u2);
-                    }
-                R coef;
-                if (type == VEL) {
-                    coef = R(-1);
-                } else {
-                    const R wa = R(0.125) * (R(1) + R(4) * gam * en);
-                    coef = wa / (R(1) - wa);
-                    a.gcn[c.n] = ckn;
-                }
-#pragma unroll
-                for (int k = 0; k < 7; ++k) s[k] = (k == kn) ? R(0) : s[k] + coef * ckn;
-            }
-        }
-        const R inv = R(1) / a.ascale;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) Pop<TA>::st(a.aout, (size_t)k * a.np + c.n, s[k] * inv, R(0));
-        if (REDUCE && type != WALL) {
-            R t = 0;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) t += fabs(s[k]);
-            acc[0] = (double)t;
-        }
-    }
-    if (REDUCE) block_partials<1>(acc, a.partials);
+    if (c.active) thermal_adjoint_node<T, TA, R, REDUCE>(a, c, acc);
+    if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
 }
 
 // thermal-to-flow coupling v/rho0 (added as e_i.v/rho0 to f*_C,i) and the
@@ -827,6 +846,159 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
     a.out0[a.np + c.n] = v1 * inv;
     a.out0[2 * a.np + c.n] = v2 * inv;
     a.out1[c.n] = sT;
+}
+
+// ---------------------------------------------------------------------------
+// batched (serving) kernels: one persistent launch walks the tiles of every
+// resident lattice in a phase.  A tile is one block of that lattice's own
+// single-lattice launch geometry (same threads, same warps), so each lattice's
+// arithmetic and partial sums are bit-identical to its single-lattice solve,
+// whatever else is resident.
+// ---------------------------------------------------------------------------
+template <typename T, typename TG, typename TA, typename R>
+struct BatchSlot {
+    FlowArgs<T, TA, R> f;
+    ThermArgs<TG, TA, R> t;
+    void* buf[4][2];   // per phase (flow, temperature, adjoint, temperature adjoint)
+    int cur[4];        // per phase: buffer read at step 0 of a graph block
+    int gx, gy, bx, by;
+};
+
+__device__ __forceinline__ Cell tile_cell(long long b, int gx, int gy, int bx, int by, int nx, int ny) {
+    const int tid = threadIdx.x;
+    const long long gxy = (long long)gx * gy;
+    const int z = (int)(b / gxy);
+    const int r = (int)(b - (long long)z * gxy);
+    const int tyb = r / gx, txb = r - tyb * gx;
+    Cell c;
+    c.x = txb * bx + (tid % bx);
+    c.y = tyb * by + (tid / bx);
+    c.z = z;
+    c.active = (tid < bx * by) && (c.x < nx) && (c.y < ny);
+    c.n = c.x + (long long)nx * (c.y + (long long)ny * c.z);
+    return c;
+}
+
+template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_batch_flow(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
+                                                    const int2* __restrict__ tiles,
+                                                    const int* __restrict__ ntiles, int step) {
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
+        FlowArgs<T, TA, R> a = S.f;
+        const int p = (S.cur[0] + step) & 1;
+        a.fin = (const T*)S.buf[0][p];
+        a.fout = (T*)S.buf[0][p ^ 1];
+        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
+        double acc[2] = {0.0, 0.0};
+        if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
+        if (REDUCE) block_partials<2>(acc, a.partials, tl.y);
+    }
+}
+
+// each slot takes the thermal-coupling variant only if it has a coupling field
+template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_batch_adjoint(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
+                                                       const int2* __restrict__ tiles,
+                                                       const int* __restrict__ ntiles, int step) {
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
+        FlowArgs<T, TA, R> a = S.f;
+        const int p = (S.cur[2] + step) & 1;
+        a.ain = (const TA*)S.buf[2][p];
+        a.aout = (TA*)S.buf[2][p ^ 1];
+        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
+        double acc[1] = {0.0};
+        if (c.active) {
+            if (a.cpl)
+                flow_adjoint_node<L, T, TA, R, REDUCE, true>(a, c, acc);
+            else
+                flow_adjoint_node<L, T, TA, R, REDUCE, false>(a, c, acc);
+        }
+        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
+    }
+}
+
+template <typename T, typename TG, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_batch_thermal(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
+                                                       const int2* __restrict__ tiles,
+                                                       const int* __restrict__ ntiles, int step) {
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
+        ThermArgs<TG, TA, R> a = S.t;
+        const int p = (S.cur[1] + step) & 1;
+        a.gin = (const TG*)S.buf[1][p];
+        a.gout = (TG*)S.buf[1][p ^ 1];
+        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
+        double acc[1] = {0.0};
+        if (c.active) thermal_step_node<TG, TA, R, REDUCE>(a, c, acc);
+        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
+    }
+}
+
+template <typename T, typename TG, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_batch_thermal_adjoint(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
+                                                               const int2* __restrict__ tiles,
+                                                               const int* __restrict__ ntiles, int step) {
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
+        ThermArgs<TG, TA, R> a = S.t;
+        const int p = (S.cur[3] + step) & 1;
+        a.ain = (const TA*)S.buf[3][p];
+        a.aout = (TA*)S.buf[3][p ^ 1];
+        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
+        double acc[1] = {0.0};
+        if (c.active) thermal_adjoint_node<TG, TA, R, REDUCE>(a, c, acc);
+        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
+    }
+}
+
+// per-lattice second stage of the batched reductions: one block per listed
+// slot sums that slot's partials in the same fixed order as k_finalize
+template <int NV, typename T, typename TG, typename TA, typename R>
+__global__ void __launch_bounds__(256) k_batch_finalize(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
+                                                        const int* __restrict__ list,
+                                                        const int* __restrict__ nlist,
+                                                        double* __restrict__ results) {
+    const int n = *nlist;
+    __shared__ double sh[NV][8];
+    for (int q = blockIdx.x; q < n; q += gridDim.x) {
+        const int slot = list[q];
+        const BatchSlot<T, TG, TA, R>& S = slots[slot];
+        const double* __restrict__ partials = S.f.partials;
+        const long long nblocks = (long long)S.gx * S.gy * S.f.nz;
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = 0.0;
+        for (long long b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] += partials[b * NV + k];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = s[k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) sh[k][warp] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                double t = lane < (int)(blockDim.x >> 5) ? sh[k][lane] : 0.0;
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+                if (lane == 0) results[2 * slot + k] = t;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // deterministic second stage of every reduction: one block sums the per-block

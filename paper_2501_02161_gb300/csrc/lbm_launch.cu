@@ -1,5 +1,7 @@
 // lbm_launch.cu -- template instantiation and dispatch of the kernels for each
 // (stencil, storage) pair.
+#include <cstring>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -198,6 +200,118 @@ cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64,
         k_convert<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)dst, n);
     else
         k_convert<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)dst, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched (serving) kernels: D3Q19 with FP32 arithmetic (storage 1, 2, 3)
+// ---------------------------------------------------------------------------
+namespace {
+template <int S>
+using SlotT = BatchSlot<typename StorageTypes<S>::T, typename StorageTypes<S>::TG,
+                        typename StorageTypes<S>::TA, typename StorageTypes<S>::R>;
+
+template <int S>
+void fill_slot(void* dst, const FlowLaunch& f, const ThermLaunch& t, void* const bufs[4][2],
+               const int cur[4], int gx, int gy, int bx, int by) {
+    SlotT<S> sl;
+    std::memset(&sl, 0, sizeof(sl));
+    sl.f = flow_args<S>(f);
+    sl.t = therm_args<S>(t);
+    for (int p = 0; p < 4; ++p) {
+        sl.buf[p][0] = bufs[p][0];
+        sl.buf[p][1] = bufs[p][1];
+        sl.cur[p] = cur[p];
+    }
+    sl.gx = gx;
+    sl.gy = gy;
+    sl.bx = bx;
+    sl.by = by;
+    std::memcpy(dst, &sl, sizeof(sl));
+}
+
+template <int S>
+void batch_dispatch(int phase, bool reduce, bool thermal, const void* slots, const int2* tiles,
+                    const int* ntiles, int step, int grid, cudaStream_t s) {
+    using T = typename StorageTypes<S>::T;
+    using TG = typename StorageTypes<S>::TG;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    const SlotT<S>* sl = (const SlotT<S>*)slots;
+    switch (phase) {
+        case 0:
+            if (reduce) k_batch_flow<D3Q19, T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            else k_batch_flow<D3Q19, T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            break;
+        case 1:
+            if (reduce) k_batch_thermal<T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            else k_batch_thermal<T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            break;
+        case 2:
+            (void)thermal;
+            if (reduce) k_batch_adjoint<D3Q19, T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            else k_batch_adjoint<D3Q19, T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            break;
+        default:
+            if (reduce) k_batch_thermal_adjoint<T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            else k_batch_thermal_adjoint<T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
+            break;
+    }
+}
+
+template <int S>
+void batch_finalize_dispatch(int nv, const void* slots, const int* list, const int* nlist,
+                             double* results, int grid, cudaStream_t s) {
+    using T = typename StorageTypes<S>::T;
+    using TG = typename StorageTypes<S>::TG;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    const SlotT<S>* sl = (const SlotT<S>*)slots;
+    if (nv == 2)
+        k_batch_finalize<2, T, TG, TA, R><<<grid, 256, 0, s>>>(sl, list, nlist, results);
+    else
+        k_batch_finalize<1, T, TG, TA, R><<<grid, 256, 0, s>>>(sl, list, nlist, results);
+}
+}  // namespace
+
+size_t batch_slot_bytes(int storage) {
+    switch (storage) {
+        case 1: return sizeof(SlotT<1>);
+        case 2: return sizeof(SlotT<2>);
+        case 3: return sizeof(SlotT<3>);
+        default: return 0;
+    }
+}
+
+void batch_fill_slot(int storage, void* dst, const FlowLaunch& f, const ThermLaunch& t,
+                     void* const bufs[4][2], const int cur[4], int gx, int gy, int bx, int by) {
+    switch (storage) {
+        case 1: fill_slot<1>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
+        case 2: fill_slot<2>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
+        case 3: fill_slot<3>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
+        default: break;
+    }
+}
+
+cudaError_t batch_launch(int storage, int phase, bool reduce, bool thermal, const void* slots,
+                         const int2* tiles, const int* ntiles, int step, int grid, cudaStream_t s) {
+    switch (storage) {
+        case 1: batch_dispatch<1>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
+        case 2: batch_dispatch<2>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
+        case 3: batch_dispatch<3>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_finalize_launch(int storage, int nv, const void* slots, const int* list,
+                                  const int* nlist, double* results, int grid, cudaStream_t s) {
+    switch (storage) {
+        case 1: batch_finalize_dispatch<1>(nv, slots, list, nlist, results, grid, s); break;
+        case 2: batch_finalize_dispatch<2>(nv, slots, list, nlist, results, grid, s); break;
+        case 3: batch_finalize_dispatch<3>(nv, slots, list, nlist, results, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <tuple>
@@ -760,6 +761,393 @@ lbm_status lbm_time_steps(lbm_ctx* c, int phase, int n, double* ms_per_step) {
     cudaEventDestroy(e1);
     *ms_per_step = (double)ms / n;
     return leave(c);
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batched solves (serving)
+// ===========================================================================
+namespace {
+
+enum SlotPhase { SP_FLOW = 0, SP_THERM = 1, SP_ADJ = 2, SP_TADJ = 3, SP_DONE = 4 };
+
+struct BatchEntry {
+    lbm_ctx* ctx = nullptr;
+    int phase = SP_DONE;
+    long long steps = 0;     // steps in the current phase
+    long long total = 0;     // steps over all phases
+    double tol = 0, res = INFINITY;
+    long long max_steps = 0;
+    int status = LBM_OK;     // worst warning / first error
+    double t0 = 0;
+    bool used = false;
+};
+
+}  // namespace
+
+struct lbm_batch {
+    int device = 0;
+    int storage = 1;
+    int K = 1000;
+    int max_slots = 0;
+    int grid = 0;
+    size_t slot_bytes = 0;
+    cudaStream_t stream = nullptr;
+    void* d_slots = nullptr;
+    std::vector<char> h_slots;
+    int2* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long tile_cap[4] = {0, 0, 0, 0};
+    int* d_lists = nullptr;  // 4 phase lists of max_slots slot ids
+    int* d_counts = nullptr; // ntiles[4], nslots[4]
+    double* d_results = nullptr;
+    double* h_results = nullptr;
+    std::vector<BatchEntry> e;
+    std::vector<std::pair<int, lbm_report>> done;
+    bool dirty = true;
+    bool any_thermal = false;
+    std::map<std::pair<int, bool>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+lbm_status batch_fail(lbm_status s, const std::string& m) { return fail(s, m); }
+
+void batch_slot_refresh(lbm_batch* b, int i) {
+    BatchEntry& en = b->e[i];
+    lbm_ctx* c = en.ctx;
+    FlowLaunch f = flow_base(c);
+    f.out0 = c->rho;
+    f.out1 = c->u;
+    ThermLaunch t = therm_base(c);
+    t.out0 = c->T;
+    t.out1 = c->gpost;
+    void* bufs[4][2] = {{c->f[0], c->f[1]}, {c->g[0], c->g[1]}, {c->fa[0], c->fa[1]}, {c->ga[0], c->ga[1]}};
+    int cur[4] = {c->fcur, c->gcur, c->facur, c->gacur};
+    batch_fill_slot(b->storage, b->h_slots.data() + (size_t)i * b->slot_bytes, f, t, bufs, cur,
+                    (int)c->geom.grid.x, (int)c->geom.grid.y, (int)c->geom.block.x, (int)c->geom.block.y);
+}
+
+// rebuild slot descriptors, per-phase tile tables and slot lists on the device
+lbm_status batch_upload(lbm_batch* b) {
+    std::vector<std::vector<int2>> tiles(4);
+    std::vector<int> lists(4 * (size_t)b->max_slots, 0);
+    int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    b->any_thermal = false;
+    for (int i = 0; i < b->max_slots; ++i) {
+        BatchEntry& en = b->e[i];
+        if (!en.used || en.phase == SP_DONE) continue;
+        batch_slot_refresh(b, i);
+        const int ph = en.phase;
+        const long long nb = en.ctx->geom.nblocks;
+        for (long long k = 0; k < nb; ++k) tiles[ph].push_back(make_int2(i, (int)k));
+        lists[(size_t)ph * b->max_slots + counts[4 + ph]++] = i;
+        if (ph == SP_ADJ && en.ctx->thermal) b->any_thermal = true;
+    }
+    for (int ph = 0; ph < 4; ++ph) {
+        counts[ph] = (int)tiles[ph].size();
+        if ((long long)tiles[ph].size() > b->tile_cap[ph]) {
+            if (b->d_tiles[ph]) CUDA_TRY(cudaFree(b->d_tiles[ph]));
+            b->d_tiles[ph] = nullptr;
+            long long cap = std::max<long long>(1024, (long long)tiles[ph].size() * 2);
+            CUDA_TRY(cudaMalloc(&b->d_tiles[ph], sizeof(int2) * cap));
+            b->tile_cap[ph] = cap;
+            // the graphs hold the old table pointers
+            for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+            b->graphs.clear();
+        }
+        if (!tiles[ph].empty())
+            CUDA_TRY(cudaMemcpyAsync(b->d_tiles[ph], tiles[ph].data(), sizeof(int2) * tiles[ph].size(),
+                                     cudaMemcpyHostToDevice, b->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_slots, b->h_slots.data(), b->slot_bytes * b->max_slots,
+                             cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(b->d_lists, lists.data(), sizeof(int) * lists.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->dirty = false;
+    return LBM_OK;
+}
+
+int batch_mask(lbm_batch* b) {
+    int m = 0;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (b->e[i].used && b->e[i].phase != SP_DONE) m |= 1 << b->e[i].phase;
+    return m;
+}
+
+cudaError_t batch_enqueue(lbm_batch* b, int mask, bool thermal_adj) {
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < b->K && e == cudaSuccess; ++s)
+        for (int ph = 0; ph < 4 && e == cudaSuccess; ++ph)
+            if (mask & (1 << ph))
+                e = batch_launch(b->storage, ph, s == b->K - 1, ph == SP_ADJ && thermal_adj, b->d_slots,
+                                 b->d_tiles[ph], b->d_counts + ph, s, b->grid, b->stream);
+    for (int ph = 0; ph < 4 && e == cudaSuccess; ++ph)
+        if (mask & (1 << ph))
+            e = batch_finalize_launch(b->storage, ph == SP_FLOW ? 2 : 1, b->d_slots,
+                                      b->d_lists + (size_t)ph * b->max_slots, b->d_counts + 4 + ph,
+                                      b->d_results, b->grid, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * 2 * b->max_slots,
+                            cudaMemcpyDeviceToHost, b->stream);
+    return e;
+}
+
+// a context moves to its next phase (or finishes); kernels it needs run on its stream
+lbm_status batch_advance(lbm_batch* b, int i, int st) {
+    BatchEntry& en = b->e[i];
+    lbm_ctx* c = en.ctx;
+    if (st < 0) {
+        en.status = st;
+        en.phase = SP_DONE;
+    } else {
+        if (st > 0 && en.status == LBM_OK) en.status = st;
+        if (en.phase == SP_FLOW) {
+            if (c->thermal) {
+                en.phase = SP_THERM;
+            } else {
+                c->fwd_done = true;
+                en.phase = SP_ADJ;
+            }
+        } else if (en.phase == SP_THERM) {
+            c->fwd_done = true;
+            en.phase = c->thermal ? SP_TADJ : SP_ADJ;
+        } else if (en.phase == SP_TADJ) {
+            ThermLaunch t = therm_base(c);
+            t.gin = c->g[c->gcur];
+            t.ain = c->ga[c->gacur];
+            t.out0 = c->cpl;
+            t.out1 = c->sT;
+            CUDA_TRY(thermal_launch(c->storage, TOP_COUPLING, t, c->geom, c->stream));
+            en.phase = SP_ADJ;
+        } else if (en.phase == SP_ADJ) {
+            c->adj_done = true;
+            c->astate = true;
+            en.phase = SP_DONE;
+        }
+        if (en.phase == SP_ADJ || en.phase == SP_TADJ) {
+            if (!c->astate) {
+                lbm_status s2 = init_adjoint(c);
+                if (s2 != LBM_OK) return s2;
+                c->astate = true;
+            }
+        }
+        en.steps = 0;
+        en.res = INFINITY;
+    }
+    if (en.phase == SP_DONE) {
+        if (en.status < 0) {
+            if (c->fwd_done == false) c->fstate = false;
+            else c->astate = false;
+        }
+        lbm_report r;
+        r.steps = en.total;
+        r.residual = en.res;
+        r.I = c->last_I[PH_ADJ];
+        r.J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        r.ms = now_ms() - en.t0;
+        r.status = en.status;
+        b->done.push_back(std::make_pair(i, r));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    b->dirty = true;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_footprint_bytes(int stencil, int nx, int ny, int nz, int storage, int thermal) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || storage < 0 || storage > 3) return 0;
+    const size_t N = (size_t)nx * ny * nz, np = (N + 63) / 64 * 64;
+    const int Q = stencil == LBM_D2Q9 ? 9 : 19;
+    const size_t pb = pop_bytes(storage), ab = adj_bytes(storage), rb = aux_bytes(storage),
+                 hb = heat_bytes(storage);
+    size_t bytes = 2 * np * Q * (pb + ab) + np * (1 + rb * (1 + 4 + 3 + 1 + 1));
+    if (thermal) bytes += 2 * np * 7 * (hb + ab) + np * rb * (1 + 7 + 3 + 1 + 1);
+    Geom g = make_geom(nx, ny, nz);
+    bytes += sizeof(double) * 2 * (size_t)g.nblocks + 64;
+    return bytes;
+}
+
+lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots) {
+    if (!out) return fail(LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (storage == LBM_FP64) return fail(LBM_ERR_UNSUPPORTED, "batches are built for FP32 arithmetic storage");
+    if (storage < LBM_FP32 || storage > LBM_BF16_OFS) return fail(LBM_ERR_ARG, "unknown storage");
+    if (check_every <= 0 || (check_every & 1)) return fail(LBM_ERR_ARG, "check_every must be positive and even");
+    if (max_slots <= 0 || max_slots > 4096) return fail(LBM_ERR_ARG, "max_slots out of range");
+    lbm_batch* b = new lbm_batch();
+    cudaGetDevice(&b->device);
+    b->storage = storage;
+    b->K = check_every;
+    b->max_slots = max_slots;
+    b->slot_bytes = batch_slot_bytes(storage);
+    b->h_slots.assign(b->slot_bytes * max_slots, 0);
+    b->e.resize(max_slots);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->grid = std::max(1, sms) * 4;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, b->slot_bytes * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_lists, sizeof(int) * 4 * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_results, sizeof(double) * 2 * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_results, sizeof(double) * 2 * max_slots);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counts, 0, sizeof(int) * 8);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (int ph = 0; ph < 4; ++ph)
+        if (b->d_tiles[ph]) cudaFree(b->d_tiles[ph]);
+    if (b->d_slots) cudaFree(b->d_slots);
+    if (b->d_lists) cudaFree(b->d_lists);
+    if (b->d_counts) cudaFree(b->d_counts);
+    if (b->d_results) cudaFree(b->d_results);
+    if (b->h_results) cudaFreeHost(b->h_results);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* c, const lbm_solve_opts* o, int* slot) {
+    if (!b || !c || !o) return fail(LBM_ERR_ARG, "null argument");
+    if (c->stencil != LBM_D3Q19) return fail(LBM_ERR_ARG, "batches hold D3Q19 contexts");
+    if (c->storage != b->storage) return fail(LBM_ERR_ARG, "context storage differs from the batch's");
+    if (o->max_steps < 0 || std::isnan(o->tol)) return fail(LBM_ERR_ARG, "bad opts");
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    int i = -1;
+    for (int k = 0; k < b->max_slots; ++k)
+        if (!b->e[k].used) {
+            i = k;
+            break;
+        }
+    if (i < 0) return fail(LBM_ERR_ARG, "batch is full");
+    if ((st = enter(c)) != LBM_OK) return st;
+    if (o->reset || !c->fstate) {
+        if ((st = init_forward(c)) != LBM_OK) return st;
+        c->fstate = true;
+    }
+    if (o->reset) c->astate = false;
+    c->fwd_done = c->adj_done = false;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    BatchEntry& en = b->e[i];
+    en = BatchEntry();
+    en.ctx = c;
+    en.used = true;
+    en.phase = SP_FLOW;
+    en.tol = o->tol;
+    en.max_steps = o->max_steps;
+    en.t0 = now_ms();
+    b->dirty = true;
+    if (slot) *slot = i;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
+    if (!b) return fail(LBM_ERR_ARG, "batch is null");
+    CUDA_TRY(cudaSetDevice(b->device));
+    // contexts whose phase has nothing to do (max_steps reached) move on first
+    for (int i = 0; i < b->max_slots; ++i) {
+        BatchEntry& en = b->e[i];
+        while (en.used && en.phase != SP_DONE && en.steps >= en.max_steps) {
+            lbm_status st = batch_advance(b, i, en.tol > 0 ? LBM_NOT_CONVERGED : LBM_OK);
+            if (st != LBM_OK) return st;
+        }
+    }
+    if (b->dirty) {
+        lbm_status st = batch_upload(b);
+        if (st != LBM_OK) return st;
+    }
+    const int mask = batch_mask(b);
+    if (mask) {
+        auto key = std::make_pair(mask, b->any_thermal);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = batch_enqueue(b, mask, b->any_thermal);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                (void)cudaGetLastError();
+                return fail(LBM_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            cudaGraphExec_t x = nullptr;
+            cudaError_t e3 = cudaGraphInstantiate(&x, g, 0);
+            cudaGraphDestroy(g);
+            if (e3 != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e3));
+            it = b->graphs.emplace(key, x).first;
+        }
+        CUDA_TRY(cudaGraphLaunch(it->second, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        for (int i = 0; i < b->max_slots; ++i) {
+            BatchEntry& en = b->e[i];
+            if (!en.used || en.phase == SP_DONE) continue;
+            lbm_ctx* c = en.ctx;
+            const int ph = en.phase;
+            // map the slot phase to the context's residual bookkeeping
+            const int cph = ph == SP_FLOW ? PH_FLOW : (ph == SP_THERM ? PH_THERM : (ph == SP_ADJ ? PH_ADJ : PH_TADJ));
+            const double* r = b->h_results + 2 * i;
+            const double denom = (double)(c->n_nw > 0 ? c->n_nw : 1);
+            const double cur = r[0] / denom;
+            if (ph == SP_FLOW) c->J_p = c->n_in > 0 ? c->obj.w_pin * r[1] / (3.0 * (double)c->n_in) : 0.0;
+            if (ph == SP_THERM) c->J_T = c->obj.w_tmean * cur;
+            en.steps += b->K;
+            en.total += b->K;
+            const bool bad = !std::isfinite(cur) || (ph == SP_FLOW && !std::isfinite(r[1]));
+            if (bad) {
+                c->last_I[cph] = cur;
+                lbm_status st = batch_advance(b, i, LBM_ERR_DIVERGED);
+                if (st != LBM_OK) return st;
+                continue;
+            }
+            en.res = rel_change(cur, c->last_I[cph]);
+            c->last_I[cph] = cur;
+            lbm_status st = LBM_OK;
+            if (en.tol > 0 && en.res < en.tol)
+                st = batch_advance(b, i, LBM_OK);
+            else if (en.steps >= en.max_steps)
+                st = batch_advance(b, i, en.tol > 0 ? LBM_NOT_CONVERGED : LBM_OK);
+            if (st != LBM_OK) return st;
+        }
+    }
+    if (n_active) {
+        int n = 0;
+        for (int i = 0; i < b->max_slots; ++i) n += b->e[i].used && b->e[i].phase != SP_DONE;
+        *n_active = n;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_poll(lbm_batch* b, int* slots, lbm_ctx** ctxs, lbm_report* reps, int max, int* n) {
+    if (!b || !n) return fail(LBM_ERR_ARG, "null argument");
+    int k = 0;
+    while (!b->done.empty() && k < max) {
+        auto pr = b->done.front();
+        b->done.erase(b->done.begin());
+        const int i = pr.first;
+        if (slots) slots[k] = i;
+        if (ctxs) ctxs[k] = b->e[i].ctx;
+        if (reps) reps[k] = pr.second;
+        b->e[i] = BatchEntry();
+        ++k;
+    }
+    *n = k;
+    return LBM_OK;
 }
 
 }  // extern "C"

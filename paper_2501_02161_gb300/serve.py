@@ -1,0 +1,349 @@
+"""Serving: continuous batching of sensitivity and optimisation-step requests.
+
+Requests of mixed lattice shapes and Re arrive over time.  The server admits
+them, in arrival order, as batch slots and HBM budget free up (admission by
+the device footprint each context needs), keeps finished designs resident so
+that an optimisation-step request on the same design warm-starts from its
+populations, and advances every resident lattice together: one
+`lbm_batch_step` is one CUDA-graph replay of persistent kernels covering all
+resident lattices for K steps.  Lattices that arrive while others run join at
+the next replay.  The baseline serves the same requests one at a time through
+the plain single-context FP32 path.  All solver work runs in the CUDA library;
+this module only schedules.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _capi as C
+from . import inputs as I
+from .solver import STORAGES, Report, Solver
+
+SHAPES = [(32, 32, 32), (64, 64, 64), (96, 48, 24), (128, 64, 32), (192, 96, 48)]
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    shape: tuple
+    re: float
+    thermal: bool
+    kind: str               # "sens" or "opt" (optimisation step on an earlier design)
+    design: int             # design id (opt requests refer to an earlier sens request's design)
+    seed: int
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    arrival: float
+    admitted: float = float("nan")
+    done: float = float("nan")
+    status: int = 0
+    steps: int = 0
+    J: float = float("nan")
+    warm: bool = False
+    sens: torch.Tensor | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def make_requests(n: int = 256, seed: int = 5, rate: float | None = None,
+                  shapes=SHAPES, opt_frac: float = 0.2, thermal_frac: float = 0.5,
+                  re_range=(10.0, 500.0)) -> list:
+    """Seeded request stream: shapes uniform over `shapes`, Re ~ U[re_range],
+    thermal with probability thermal_frac, a fraction opt_frac of
+    optimisation-step requests on earlier designs, Poisson arrivals at `rate`
+    requests per second (all at t=0 when rate is None)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    sens_ids = []
+    for k in range(n):
+        if rate:
+            t += rng.exponential(1.0 / rate)
+        if sens_ids and rng.random() < opt_frac:
+            base = reqs[sens_ids[rng.integers(len(sens_ids))]]
+            reqs.append(Request(k, t, base.shape, base.re, base.thermal, "opt", base.design, base.seed))
+        else:
+            shape = shapes[rng.integers(len(shapes))]
+            reqs.append(Request(k, t, tuple(shape), float(rng.uniform(*re_range)),
+                                bool(rng.random() < thermal_frac), "sens", k, int(rng.integers(1 << 30))))
+            sens_ids.append(k)
+    return reqs
+
+
+def lattice_for(req: Request):
+    nx, ny, nz = req.shape
+    if req.thermal:
+        return I.heat_sink(nx=nx, ny=ny, nz=nz, re=req.re, seed=req.seed % 100000)
+    return I.pipe_bend_3d(n=nx, ny=ny, nz=nz, width=max(2, min(ny, nz) // 4), re=req.re,
+                          seed=req.seed % 100000)
+
+
+def footprint(lat, storage: str) -> int:
+    return int(C.lib().lbm_footprint_bytes(lat.stencil, lat.nx, lat.ny, lat.nz,
+                                           STORAGES[storage], int(lat.thermal)))
+
+
+def opt_step_gamma(lat, gamma: torch.Tensor, sens: torch.Tensor, step: float = 0.05) -> torch.Tensor:
+    """One projected-gradient update of the design nodes (fluid nodes)."""
+    design = torch.as_tensor((lat.flags & 7) == I.FLUID, device=gamma.device)
+    g = sens.to(gamma.dtype)
+    scale = g[design].abs().max().clamp_min(1e-30)
+    return torch.where(design, (gamma - step * g / scale).clamp(0.0, 1.0), gamma)
+
+
+class Batch:
+    """Thin owner of an lbm_batch (same names as the C-ABI)."""
+
+    def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 64):
+        self.lib = C.lib()
+        self._b = ctypes.c_void_p()
+        C.check(self.lib.lbm_batch_create(ctypes.byref(self._b), STORAGES[storage],
+                                          int(check_every), int(max_slots)), "lbm_batch_create")
+        self.max_slots = max_slots
+        self._slots = (ctypes.c_int * max_slots)()
+        self._ctxs = (ctypes.c_void_p * max_slots)()
+        self._reps = (C.lbm_report * max_slots)()
+
+    def admit(self, solver: Solver, tol: float, max_steps: int, reset: bool) -> int:
+        o = C.lbm_solve_opts(float(tol), int(max_steps), 0, int(reset))
+        slot = ctypes.c_int()
+        C.check(self.lib.lbm_batch_admit(self._b, solver._ctx, ctypes.byref(o), ctypes.byref(slot)),
+                "lbm_batch_admit")
+        return slot.value
+
+    def step(self) -> int:
+        n = ctypes.c_int()
+        C.check(self.lib.lbm_batch_step(self._b, ctypes.byref(n)), "lbm_batch_step")
+        return n.value
+
+    def poll(self):
+        n = ctypes.c_int()
+        C.check(self.lib.lbm_batch_poll(self._b, self._slots, self._ctxs, self._reps,
+                                        self.max_slots, ctypes.byref(n)), "lbm_batch_poll")
+        out = []
+        for k in range(n.value):
+            r = self._reps[k]
+            out.append((self._slots[k], self._ctxs[k],
+                        Report(r.steps, r.residual, r.I, r.J, r.ms, r.status)))
+        return out
+
+    def close(self):
+        if self._b:
+            self.lib.lbm_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over one GPU."""
+
+    def __init__(self, storage: str = "fp32", budget_bytes: int | None = None,
+                 check_every: int = 500, max_slots: int = 64, tol: float = 1e-4,
+                 max_steps: int = 20000, keep_designs: bool = True, device=None):
+        self.device = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
+        self.storage = storage
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(free * 0.8)
+        self.budget = budget_bytes
+        self.used = 0
+        self.tol, self.max_steps = tol, max_steps
+        self.keep = keep_designs
+        self.batch = Batch(storage, check_every, max_slots)
+        self.max_slots = max_slots
+        self.resident = OrderedDict()   # design id -> (solver, lattice, gamma, last sens, bytes)
+        self.active = {}                # ctx pointer value -> (request, result, design id)
+
+    def _evict_one(self) -> bool:
+        busy = {d for (_, _, d) in self.active.values()}
+        for d in list(self.resident):
+            if d not in busy:
+                s, _, _, _, nb = self.resident.pop(d)
+                s.close()
+                self.used -= nb
+                return True
+        return False
+
+    def _admit(self, req: Request, res: Result, now: float) -> bool:
+        if len(self.active) >= self.max_slots:
+            return False
+        d = req.design
+        warm = False
+        if any(dd == d for (_, _, dd) in self.active.values()):
+            return False  # that design is still being solved: its next request waits
+        if req.kind == "opt" and d in self.resident and self.resident[d][3] is not None:
+            s, lat, gamma, sens, nb = self.resident[d]
+            self.resident.move_to_end(d)
+            gamma = opt_step_gamma(lat, gamma, sens)
+            s.set_gamma(gamma)
+            self.resident[d] = (s, lat, gamma, sens, nb)
+            warm = True
+        else:
+            lat = lattice_for(req)
+            nb = footprint(lat, self.storage)
+            while self.used + nb > self.budget:
+                if not self._evict_one():
+                    return False
+            s = Solver.from_lattice(lat, storage=self.storage, device=self.device)
+            gamma = torch.as_tensor(lat.gamma, dtype=s.rdtype, device=self.device)
+            if req.kind == "opt":
+                # design not resident any more: replay its update from a cold state
+                gamma = gamma.clone()
+            if d in self.resident:
+                old = self.resident.pop(d)
+                old[0].close()
+                self.used -= old[4]
+            self.resident[d] = (s, lat, gamma, None, nb)
+            self.used += nb
+        self.batch.admit(s, self.tol, self.max_steps, reset=not warm)
+        res.admitted = now
+        res.warm = warm
+        self.active[s._ctx.value] = (req, res, d)
+        return True
+
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (arrival times in seconds from now); returns results."""
+        order = deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = deque()
+        results = {r.rid: Result(r.rid, r.kind, r.arrival) for r in requests}
+        t0 = time.perf_counter()
+        done = 0
+        while done < len(requests):
+            now = time.perf_counter() - t0 if realtime else float("inf")
+            while order and order[0].arrival <= now:
+                waiting.append(order.popleft())
+            # admission: arrival order, except that a request whose design is
+            # still being solved lets later requests for other designs pass;
+            # the first request that does not fit in memory stops admission
+            blocked = set()
+            kept = deque()
+            while waiting:
+                req = waiting.popleft()
+                if req.design in blocked:
+                    kept.append(req)
+                    continue
+                busy = any(dd == req.design for (_, _, dd) in self.active.values())
+                if busy:
+                    blocked.add(req.design)
+                    kept.append(req)
+                    continue
+                if not self._admit(req, results[req.rid], time.perf_counter() - t0):
+                    kept.append(req)
+                    kept.extend(waiting)
+                    waiting.clear()
+                    break
+            waiting = kept
+            if not self.active:
+                if order and realtime:
+                    time.sleep(max(0.0, order[0].arrival - (time.perf_counter() - t0)))
+                continue
+            self.batch.step()
+            for slot, ctx, rep in self.batch.poll():
+                req, res, d = self.active.pop(ctx)
+                s = self.resident[d][0]
+                res.status = rep.status
+                res.steps = rep.steps
+                res.J = rep.J
+                if rep.status >= 0:
+                    sens = s.sensitivity(dtype=torch.float32)
+                    res.sens = sens
+                    ent = self.resident[d]
+                    self.resident[d] = (ent[0], ent[1], ent[2], sens, ent[4])
+                torch.cuda.synchronize(self.device)
+                res.done = time.perf_counter() - t0
+                done += 1
+                if not self.keep or rep.status < 0:
+                    ent = self.resident.pop(d)
+                    ent[0].close()
+                    self.used -= ent[4]
+        return [results[r.rid] for r in requests]
+
+    def close(self):
+        for d in list(self.resident):
+            self.resident.pop(d)[0].close()
+        self.batch.close()
+
+
+def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_steps: int = 20000,
+                     check_every: int = 500, realtime: bool = True, keep_designs: bool = True,
+                     device=None):
+    """Baseline: one request at a time, in arrival order, through the
+    single-context solver (plain path, same tolerance and step caps)."""
+    dev = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
+    designs = OrderedDict()
+    results = []
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        if realtime:
+            wait = req.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        res = Result(req.rid, req.kind, req.arrival, admitted=time.perf_counter() - t0)
+        warm = False
+        if req.kind == "opt" and req.design in designs and designs[req.design][3] is not None:
+            s, lat, gamma, sens = designs[req.design]
+            gamma = opt_step_gamma(lat, gamma, sens)
+            s.set_gamma(gamma)
+            warm = True
+        else:
+            lat = lattice_for(req)
+            if req.design in designs:
+                designs.pop(req.design)[0].close()
+            s = Solver.from_lattice(lat, storage=storage, device=dev)
+            gamma = torch.as_tensor(lat.gamma, dtype=s.rdtype, device=dev)
+        rf = s.forward(tol=tol, max_steps=max_steps, check_every=check_every, reset=not warm,
+                       strict=False)
+        sens = None
+        rep_status, steps = rf.status, rf.steps
+        if rf.status >= 0:
+            ra = s.adjoint(tol=tol, max_steps=max_steps, check_every=check_every,
+                           reset=not warm, strict=False)
+            steps += ra.steps
+            if ra.status >= 0:
+                sens = s.sensitivity(dtype=torch.float32)
+                rep_status = max(rf.status, ra.status)
+            else:
+                rep_status = ra.status
+        torch.cuda.synchronize(dev)
+        res.done = time.perf_counter() - t0
+        res.status, res.steps, res.J, res.sens, res.warm = rep_status, steps, rf.J, sens, warm
+        results.append(res)
+        if keep_designs and rep_status >= 0:
+            designs[req.design] = (s, lat, gamma, sens)
+            while len(designs) > 16:
+                designs.popitem(last=False)[1][0].close()
+        else:
+            s.close()
+    for v in designs.values():
+        v[0].close()
+    return sorted(results, key=lambda r: r.rid)
+
+
+def summarize(results, wall: float | None = None) -> dict:
+    ok = [r for r in results if r.status >= 0]
+    lat = np.array([r.latency for r in results])
+    wall = wall if wall is not None else max(r.done for r in results)
+    return {"requests": len(results), "completed": len(ok),
+            "failed": len(results) - len(ok),
+            "sens_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 3),
+            "p50_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_s": round(float(np.percentile(lat, 99)), 4),
+            "mean_s": round(float(lat.mean()), 4)}

@@ -1,0 +1,121 @@
+"""Batched solves and the continuous-batching server.
+
+Each context's result must be the same alone and in any mix (the batched
+kernels run each lattice's own launch geometry and reductions, so the results
+are compared bit for bit), the same as through the single-context calls, and
+the server must give the same answers as the one-at-a-time baseline.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2501_02161_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+K = 200
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_02161_gb300 import build as B
+    B.build()
+
+
+def mix():
+    return [I.pipe_bend_3d(n=24, width=6, re=20.0, seed=2),
+            I.heat_sink(nx=32, ny=16, nz=12, re=20.0, q_flux=2e-3, seed=4),
+            I.six_port_box(),
+            I.pipe_bend_3d(n=32, width=8, re=40.0, seed=3, ny=24, nz=20),
+            I.heat_sink(nx=40, ny=20, nz=12, re=15.0, q_flux=2e-3, seed=6)]
+
+
+def solve_batched(lats, storage="fp32", tol=1e-5, max_steps=20000, order=None):
+    from paper_2501_02161_gb300.serve import Batch
+    from paper_2501_02161_gb300.solver import Solver
+    b = Batch(storage, K, 8)
+    solvers = [Solver.from_lattice(l, storage=storage) for l in lats]
+    for k in (order or range(len(lats))):
+        b.admit(solvers[k], tol, max_steps, reset=True)
+    reps = {}
+    while len(reps) < len(lats):
+        b.step()
+        for slot, ctx, rep in b.poll():
+            k = [s._ctx.value for s in solvers].index(ctx)
+            reps[k] = rep
+    out = []
+    for k, s in enumerate(solvers):
+        out.append((reps[k], s.sensitivity(dtype=torch.float64).cpu(), s.fields(torch.float64)[1].cpu()))
+        s.close()
+    b.close()
+    return out
+
+
+def test_batched_equals_single_context_bitwise():
+    from paper_2501_02161_gb300.solver import Solver
+    lats = mix()
+    got = solve_batched(lats)
+    for lat, (rep, sens, u) in zip(lats, got):
+        s = Solver.from_lattice(lat, storage="fp32")
+        rf = s.forward(tol=1e-5, max_steps=20000, check_every=K)
+        ra = s.adjoint(tol=1e-5, max_steps=20000, check_every=K)
+        assert rep.status == 0 and rep.steps == rf.steps + ra.steps
+        assert torch.equal(s.sensitivity(dtype=torch.float64).cpu(), sens), lat.name
+        assert torch.equal(s.fields(torch.float64)[1].cpu(), u), lat.name
+        assert rep.J == rf.J
+        s.close()
+
+
+def test_alone_and_in_the_mix_are_identical():
+    lats = mix()
+    together = solve_batched(lats, order=[4, 2, 0, 3, 1])
+    for k, lat in enumerate(lats):
+        alone = solve_batched([lat])[0]
+        assert alone[0].steps == together[k][0].steps
+        assert torch.equal(alone[1], together[k][1]), lat.name
+
+
+def _reqs():
+    from paper_2501_02161_gb300.serve import make_requests
+    return make_requests(14, seed=7, rate=None, shapes=[(24, 24, 24), (32, 16, 16), (40, 20, 12)],
+                         re_range=(5.0, 60.0))
+
+
+def test_server_admission_respects_the_hbm_budget():
+    from paper_2501_02161_gb300.serve import Server, footprint, lattice_for, summarize
+    reqs = _reqs()
+    biggest = max(footprint(lattice_for(r), "fp32") for r in reqs)
+    srv = Server("fp32", budget_bytes=int(2.5 * biggest), check_every=K, max_slots=8,
+                 tol=1e-5, max_steps=20000)
+    peak, conc = [], []
+    orig = srv.batch.step
+
+    def step():
+        peak.append(srv.used)
+        conc.append(len(srv.active))
+        return orig()
+    srv.batch.step = step
+    served = srv.run(reqs, realtime=False)
+    srv.close()
+    assert max(peak) <= 2.5 * biggest
+    assert max(conc) >= 2          # lattices did run together
+    summ = summarize(served)
+    assert summ["completed"] + summ["failed"] == len(reqs)
+
+
+def test_server_matches_sequential_bitwise():
+    from paper_2501_02161_gb300.serve import Server, serve_sequential
+    reqs = _reqs()
+    srv = Server("fp32", check_every=K, max_slots=8, tol=1e-5, max_steps=20000)
+    served = srv.run(reqs, realtime=False)
+    srv.close()
+    seq = serve_sequential(reqs, "fp32", tol=1e-5, max_steps=20000, check_every=K, realtime=False)
+    assert any(r.kind == "opt" and r.warm for r in served)
+    for a, b in zip(served, seq):
+        assert (a.status, a.warm) == (b.status, b.warm), (a.rid, a.status, b.status)
+        if a.status >= 0:
+            assert a.steps == b.steps, (a.rid, a.steps, b.steps)
+            assert torch.equal(a.sens.cpu(), b.sens.cpu()), a.rid
