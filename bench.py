@@ -50,11 +50,13 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cap", type=int, default=CAP,
                    help="step cap per solve phase (lower it only for profiler launch lists)")
-    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd"],
+    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve"],
                    help="kernels: time the fused step kernels on a --roof-n lattice; "
                         "precision: heat sink in FP64/FP32/FP16/BF16 storage, error per field; "
                         "autograd: the filtered / projected gradient loop")
     p.add_argument("--iters", type=int, default=50, help="autograd mode: optimisation iterations")
+    p.add_argument("--nreq", type=int, default=16, help="served requests per stream (serve mode: 256)")
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
@@ -129,6 +131,76 @@ def run_autograd(args):
                       "s_per_iter": round(dt / args.iters, 3),
                       "J": [round(h["J"], 6) for h in hist],
                       "loss": [round(h["loss"], 6) for h in hist]}))
+
+
+def run_serve(args, nreq=None, device="cuda:0"):
+    """Config-5 style serving: seeded sensitivity / optimisation-step requests
+    over 32^3 ... 192x96x48 lattices, half thermal, 20 % optimisation steps,
+    forward + adjoint to 1e-4 (20000-step cap per phase).  Two streams:
+    "as_specified" with Re ~ U[10, 500] (most requests diverge with BGK at
+    these inlet widths; they count as failed) and "stable_re" with
+    Re ~ U[10, 80] (the paper's 3D maximum was 80).
+    offline: all requests at t=0 through (a) the sequential plain-FP32 path,
+    (b) the batched FP32 server, (c) the batched server with FP16 flow storage.
+    online (stable stream): Poisson arrivals at 0.8 x the batched FP32 offline
+    request rate, through all three.  Latency = completion - arrival;
+    sens/s = completed requests / wall time."""
+    import numpy as np
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300.serve import Server, make_requests, serve_sequential, summarize
+
+    B.build()
+    n = nreq or args.nreq
+    tol, cap, K = 1e-4, 20000, 500
+
+    def agree(res, ref):
+        errs = []
+        for a, b in zip(res, ref):
+            if a.status == 0 and b.status == 0 and a.sens is not None and b.sens is not None:
+                errs.append(float(torch.linalg.norm(a.sens - b.sens) /
+                                  torch.linalg.norm(b.sens).clamp_min(1e-30)))
+        return {"median": float(np.median(errs)) if errs else None,
+                "max": float(np.max(errs)) if errs else None, "n": len(errs)}
+
+    def warm():
+        # one-time costs (module loading, first allocations, graph captures of
+        # the batch) are paid here, outside every timed run
+        w = make_requests(4, seed=11, rate=None, re_range=(10.0, 40.0),
+                          shapes=[(32, 32, 32), (64, 64, 64)])
+        serve_sequential(w, "fp32", tol=tol, max_steps=cap, check_every=K, realtime=False,
+                         device=device)
+        for storage in ("fp32", "fp16"):
+            srv = Server(storage, check_every=K, max_slots=64, tol=tol, max_steps=cap, device=device)
+            srv.run(w, realtime=False)
+            srv.close()
+
+    def run_all(reqs, realtime):
+        res = {}
+        res["sequential_fp32"] = serve_sequential(reqs, "fp32", tol=tol, max_steps=cap,
+                                                  check_every=K, realtime=realtime, device=device)
+        for storage in ("fp32", "fp16"):
+            srv = Server(storage, check_every=K, max_slots=64, tol=tol, max_steps=cap, device=device)
+            res[f"batched_{storage}"] = srv.run(reqs, realtime=realtime)
+            srv.close()
+        summ = {k: summarize(v) for k, v in res.items()}
+        for k in ("batched_fp32", "batched_fp16"):
+            summ[k]["dJdgamma_rel_l2_vs_sequential_fp32"] = agree(res[k], res["sequential_fp32"])
+        return summ
+
+    out = {"requests_per_stream": n, "tol": tol, "max_steps_per_phase": cap, "check_every": K,
+           "shapes": "32^3, 64^3, 96x48x24, 128x64x32, 192x96x48", "thermal_fraction": 0.5,
+           "opt_step_fraction": 0.2}
+    warm()
+    out["as_specified_re_10_500"] = {"offline": run_all(make_requests(n, seed=5, rate=None), False)}
+    stable = {"offline": run_all(make_requests(n, seed=5, rate=None, re_range=(10.0, 80.0)), False)}
+    off = stable["offline"]["batched_fp32"]
+    rate = 0.8 * n / max(off["wall_s"], 1e-9)
+    stable["online_rate_per_s"] = round(rate, 3)
+    stable["online"] = run_all(make_requests(n, seed=5, rate=rate, re_range=(10.0, 80.0)), True)
+    out["stable_re_10_80"] = stable
+    return out
 
 
 def run_kernels(args):
@@ -353,6 +425,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, lats, dev)
 
+    served = None
+    if not args.no_serve:
+        served = run_serve(args, device=dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(lats[RES[1]], fwd_steps=20, adj_steps=6)
@@ -373,7 +449,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "per_re": {str(k): v for k, v in per.items()},
             "roofline": roof, "roofline_at_workload": at_workload,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "served": served,
             "gpu_launches": int(total_launch),
         }
         print(json.dumps(line))
@@ -511,5 +587,9 @@ if __name__ == "__main__":
         run_precision(a)
     elif a.mode == "autograd":
         run_autograd(a)
+    elif a.mode == "serve":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"mode": "serve", **run_serve(a, nreq=a.nreq)}))
     else:
         run_ours(a)

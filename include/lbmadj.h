@@ -182,12 +182,14 @@ lbm_status lbm_get_objective(lbm_ctx* ctx, double* J);
  * 7*n values.  Either may be null. */
 lbm_status lbm_get_adjoint(lbm_ctx* ctx, void* fstar, void* gstar, int dtype, int on_device);
 
-/* Time n plain fused steps of one phase on the context's stream with CUDA
- * events recorded on that stream (after all queued work) and write the mean
- * milliseconds per launch.  phase: 0 flow forward, 1 temperature forward,
- * 2 flow adjoint, 3 temperature adjoint.  The steps advance that phase's state
- * exactly as a solve would; no reduction runs.  Needs the inputs set
- * (LBM_ERR_ORDER) and, for phases 1-3, a completed lbm_forward. */
+/* Time plain fused steps of one phase: n steps (rounded up to even) are
+ * captured as a CUDA graph, replayed once untimed, then replayed between two
+ * CUDA events recorded on the context's stream; writes the mean milliseconds
+ * per step of the timed replay (kernel time plus the gaps between graph
+ * nodes).  phase: 0 flow forward, 1 temperature forward, 2 flow adjoint,
+ * 3 temperature adjoint.  The 2n steps advance that phase's state as a solve
+ * would; no reduction runs.  Needs the inputs set (LBM_ERR_ORDER) and, for
+ * phases 1-3, a completed lbm_forward. */
 lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
 
 /* ---------------------------------------------------------------------------

@@ -203,6 +203,16 @@ __device__ __forceinline__ long long shifted(const Cell& c, int i, int s, int nx
     return x + (long long)nx * (y + (long long)ny * z);
 }
 
+// Programmatic dependent launch (sm_90+): a step kernel lets the next step's
+// grid be scheduled as soon as all of its own blocks are running, and waits
+// for the previous grid (completion and memory visibility) before it touches
+// any population or output buffer.  Outside a programmatic launch both are
+// no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ long long grid_block_id() {
     return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
 }
@@ -419,6 +429,8 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
 
 template <class L, typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_flow_step(FlowArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[2] = {0.0, 0.0};
     if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
@@ -480,10 +492,12 @@ __device__ __forceinline__ void pull_adjoint(const FlowArgs<T, TA, R>& a, const 
 
 // resident 256-thread blocks per SM requested from the compiler: the plain
 // FP32-math D3Q19 adjoint fits 40 registers without spilling (6 blocks, 75 %
-// occupancy); other variants keep the compiler's choice
-template <class L, typename R, bool HOT>
+// occupancy), its thermal-coupling variant 48 (5 blocks); the reducing
+// variants (one step in K) keep the compiler's choice
+template <class L, typename R, bool REDUCE, bool THERMAL>
 struct AdjMinBlocks {
-    static constexpr int value = (L::Q == 19 && sizeof(R) == 4 && HOT) ? 6 : 1;
+    static constexpr int value =
+        (L::Q == 19 && sizeof(R) == 4 && !REDUCE) ? (THERMAL ? 5 : 6) : 1;
 };
 
 template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
@@ -537,8 +551,10 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
 }
 
 template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
-__global__ void __launch_bounds__(256, (AdjMinBlocks<L, R, !REDUCE && !THERMAL>::value))
+__global__ void __launch_bounds__(256, (AdjMinBlocks<L, R, REDUCE, THERMAL>::value))
     k_flow_adjoint(FlowArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
     if (c.active) flow_adjoint_node<L, T, TA, R, REDUCE, THERMAL>(a, c, acc);
@@ -672,6 +688,8 @@ __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, 
 
 template <typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_thermal_step(ThermArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
     if (c.active) thermal_step_node<T, TA, R, REDUCE>(a, c, acc);
@@ -767,6 +785,8 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
 
 template <typename T, typename TA, typename R, bool REDUCE>
 __global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
     if (c.active) thermal_adjoint_node<T, TA, R, REDUCE>(a, c, acc);

@@ -102,6 +102,23 @@ therm_args(const ThermLaunch& l) {
 
 inline dim3 flat_grid(long long np) { return dim3((unsigned)((np + 255) / 256)); }
 
+// launch a step kernel as a programmatic dependent of the previous kernel in
+// the stream (the kernel waits for it with griddepcontrol.wait)
+template <typename Arg>
+void launch_pdl(void (*kernel)(Arg), const Geom& g, cudaStream_t s, const Arg& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g.grid;
+    cfg.blockDim = g.block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <class L, int S>
 void flow_dispatch(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t s) {
     using T = typename StorageTypes<S>::T;
@@ -111,12 +128,12 @@ void flow_dispatch(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t s
     switch (op) {
         case FOP_INIT_F: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
         case FOP_INIT_A: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
-        case FOP_STEP: k_flow_step<L, T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_STEP_RED: k_flow_step<L, T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_ADJ: k_flow_adjoint<L, T, TA, R, false, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_ADJ_RED: k_flow_adjoint<L, T, TA, R, true, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_ADJ_T: k_flow_adjoint<L, T, TA, R, false, true><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_ADJ_T_RED: k_flow_adjoint<L, T, TA, R, true, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_STEP: launch_pdl(k_flow_step<L, T, TA, R, false>, g, s, a); break;
+        case FOP_STEP_RED: launch_pdl(k_flow_step<L, T, TA, R, true>, g, s, a); break;
+        case FOP_ADJ: launch_pdl(k_flow_adjoint<L, T, TA, R, false, false>, g, s, a); break;
+        case FOP_ADJ_RED: launch_pdl(k_flow_adjoint<L, T, TA, R, true, false>, g, s, a); break;
+        case FOP_ADJ_T: launch_pdl(k_flow_adjoint<L, T, TA, R, false, true>, g, s, a); break;
+        case FOP_ADJ_T_RED: launch_pdl(k_flow_adjoint<L, T, TA, R, true, true>, g, s, a); break;
         case FOP_SENS: k_flow_sens<L, T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
         case FOP_SENS_T: k_flow_sens<L, T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
     }
@@ -131,10 +148,10 @@ void therm_dispatch(ThermOp op, const ThermLaunch& l, const Geom& g, cudaStream_
     switch (op) {
         case TOP_INIT_G: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
         case TOP_INIT_A: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
-        case TOP_STEP: k_thermal_step<T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case TOP_STEP_RED: k_thermal_step<T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
-        case TOP_ADJ: k_thermal_adjoint<T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case TOP_ADJ_RED: k_thermal_adjoint<T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_STEP: launch_pdl(k_thermal_step<T, TA, R, false>, g, s, a); break;
+        case TOP_STEP_RED: launch_pdl(k_thermal_step<T, TA, R, true>, g, s, a); break;
+        case TOP_ADJ: launch_pdl(k_thermal_adjoint<T, TA, R, false>, g, s, a); break;
+        case TOP_ADJ_RED: launch_pdl(k_thermal_adjoint<T, TA, R, true>, g, s, a); break;
         case TOP_COUPLING: k_thermal_coupling<T, TA, R><<<g.grid, g.block, 0, s>>>(a); break;
     }
 }

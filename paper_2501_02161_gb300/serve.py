@@ -66,12 +66,13 @@ def make_requests(n: int = 256, seed: int = 5, rate: float | None = None,
     optimisation-step requests on earlier designs, Poisson arrivals at `rate`
     requests per second (all at t=0 when rate is None)."""
     rng = np.random.default_rng(seed)
+    arr = np.random.default_rng([seed, 1])   # arrivals: own stream, contents do not depend on rate
     t = 0.0
     reqs = []
     sens_ids = []
     for k in range(n):
         if rate:
-            t += rng.exponential(1.0 / rate)
+            t += arr.exponential(1.0 / rate)
         if sens_ids and rng.random() < opt_frac:
             base = reqs[sens_ids[rng.integers(len(sens_ids))]]
             reqs.append(Request(k, t, base.shape, base.re, base.thermal, "opt", base.design, base.seed))
@@ -157,7 +158,8 @@ class Server:
 
     def __init__(self, storage: str = "fp32", budget_bytes: int | None = None,
                  check_every: int = 500, max_slots: int = 64, tol: float = 1e-4,
-                 max_steps: int = 20000, keep_designs: bool = True, device=None):
+                 max_steps: int = 20000, keep_designs: bool = True, device=None,
+                 max_active_nodes: int = 6_000_000):
         self.device = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
         self.storage = storage
         if budget_bytes is None:
@@ -167,6 +169,9 @@ class Server:
         self.used = 0
         self.tol, self.max_steps = tol, max_steps
         self.keep = keep_designs
+        # beyond a few million resident nodes one graph replay already keeps
+        # every SM busy; admitting more only lengthens everyone's latency
+        self.max_active_nodes = max_active_nodes
         self.batch = Batch(storage, check_every, max_slots)
         self.max_slots = max_slots
         self.resident = OrderedDict()   # design id -> (solver, lattice, gamma, last sens, bytes)
@@ -182,8 +187,13 @@ class Server:
                 return True
         return False
 
+    def _active_nodes(self) -> int:
+        return sum(int(np.prod(r.shape)) for (r, _, _) in self.active.values())
+
     def _admit(self, req: Request, res: Result, now: float) -> bool:
         if len(self.active) >= self.max_slots:
+            return False
+        if self.active and self._active_nodes() + int(np.prod(req.shape)) > self.max_active_nodes:
             return False
         d = req.design
         warm = False
