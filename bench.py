@@ -34,6 +34,12 @@ FWD_BYTES = {"fp32": 19 * 4 * 2 + 4 + 1, "fp64": 19 * 8 * 2 + 8 + 1,
              "fp16": 19 * 2 * 2 + 4 + 1, "bf16": 19 * 2 * 2 + 4 + 1}
 ADJ_BYTES = {"fp32": 19 * 4 * 2 + 12 + 4 + 1, "fp64": 19 * 8 * 2 + 24 + 8 + 1,
              "fp16": 19 * 4 * 2 + 12 + 4 + 1, "bf16": 19 * 4 * 2 + 12 + 4 + 1}
+THERM_BYTES = 7 * 4 * 2 + 12 + 4 + 1   # D3Q7 FP32 populations + frozen u + gamma + flag
+# DRAM bytes per node per launch (dram__bytes_read.sum + dram__bytes_write.sum
+# / nodes) from one ncu capture of the current kernels on a 160^3 pipe bend
+# (profiles/k_flow_*_pipe_bend_160cubed_fp32.md); traffic grows with the node
+# count, so a launch on N nodes moves N times this.
+TRAFFIC_B_PER_NODE = {("adjoint", "fp32"): 157.4, ("forward", "fp32"): 145.7}
 
 
 def parse():
@@ -46,6 +52,8 @@ def parse():
     p.add_argument("--storage", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     p.add_argument("--roof-n", type=int, default=320, help="edge of the >L2 roofline lattice")
     p.add_argument("--roof-launches", type=int, default=20)
+    p.add_argument("--lattice", default="pipe", choices=["pipe", "heatsink"],
+                   help="kernels mode: pipe bend (flow kernels) or heat sink (all four)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cap", type=int, default=CAP,
@@ -172,7 +180,7 @@ def run_serve(args, nreq=None, device="cuda:0"):
         serve_sequential(w, "fp32", tol=tol, max_steps=cap, check_every=K, realtime=False,
                          device=device)
         for storage in ("fp32", "fp16"):
-            srv = Server(storage, check_every=K, max_slots=64, tol=tol, max_steps=cap, device=device)
+            srv = Server(storage, check_every=K, max_slots=32, tol=tol, max_steps=cap, device=device)
             srv.run(w, realtime=False)
             srv.close()
 
@@ -181,7 +189,7 @@ def run_serve(args, nreq=None, device="cuda:0"):
         res["sequential_fp32"] = serve_sequential(reqs, "fp32", tol=tol, max_steps=cap,
                                                   check_every=K, realtime=realtime, device=device)
         for storage in ("fp32", "fp16"):
-            srv = Server(storage, check_every=K, max_slots=64, tol=tol, max_steps=cap, device=device)
+            srv = Server(storage, check_every=K, max_slots=32, tol=tol, max_steps=cap, device=device)
             res[f"batched_{storage}"] = srv.run(reqs, realtime=realtime)
             srv.close()
         summ = {k: summarize(v) for k, v in res.items()}
@@ -215,18 +223,28 @@ def run_kernels(args):
     B.build()
     torch.cuda.set_device(0)
     hbm, kind = peaks()
-    big = I.pipe_bend_3d(n=args.roof_n, re=100.0, seed=1)
+    if args.lattice == "heatsink":
+        n = args.roof_n
+        big = I.heat_sink(nx=n, ny=n // 2, nz=n // 4, re=50.0, seed=4)
+    else:
+        big = I.pipe_bend_3d(n=args.roof_n, re=100.0, seed=1)
     sb = Solver.from_lattice(big, storage=args.storage, device="cuda:0")
     sb.forward(tol=0, max_steps=2, check_every=2, reset=True)
     sb.time_steps(0, 3)
     fwd_ms = sb.time_steps(0, args.roof_launches)
+    rows = [("forward", fwd_ms, FWD_BYTES[args.storage])]
+    if big.thermal:
+        sb.time_steps(1, 3)
+        rows.append(("thermal_forward", sb.time_steps(1, args.roof_launches), THERM_BYTES))
+        sb.time_steps(3, 3)
+        rows.append(("thermal_adjoint", sb.time_steps(3, args.roof_launches), THERM_BYTES))
     sb.time_steps(2, 3)
     adj_ms = sb.time_steps(2, args.roof_launches)
+    rows.append(("adjoint", adj_ms, ADJ_BYTES[args.storage] + (12 if big.thermal else 0)))
     nb = big.n
-    out = {"mode": "kernels", "lattice": [args.roof_n] * 3, "storage": args.storage,
-           "nodes": nb, "peak_GB/s": hbm, "peak_kind": kind}
-    for name, ms, bpn in (("forward", fwd_ms, FWD_BYTES[args.storage]),
-                          ("adjoint", adj_ms, ADJ_BYTES[args.storage])):
+    out = {"mode": "kernels", "lattice": [big.nx, big.ny, big.nz], "workload": big.name,
+           "storage": args.storage, "nodes": nb, "peak_GB/s": hbm, "peak_kind": kind}
+    for name, ms, bpn in rows:
         gbs = bpn * nb / (ms * 1e-3) / 1e9
         out[name] = {"ms_per_launch": ms, "bytes_per_node": bpn, "GB/s": round(gbs, 1),
                      "frac": round(gbs / hbm, 4), "MLUPS": round(nb / (ms * 1e-3) / 1e6, 1)}
@@ -407,8 +425,13 @@ def run_ours(args):
         ms = adj_ms if kern == "adjoint" else fwd_ms
         byts = (ADJ_BYTES if kern == "adjoint" else FWD_BYTES)[args.storage] * nb
         ach = byts / (ms * 1e-3) / 1e9
+        tpn = TRAFFIC_B_PER_NODE.get((kern, args.storage))
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                "frac": round(ach / hbm, 4),
+                "traffic": round(tpn * nb) if tpn else None,
+                "traffic_note": ("bytes per launch, ncu DRAM bytes per node at 160^3 x nodes"
+                                 if tpn else None),
+                "peak_kind": peak_kind,
                 "kernel": f"k_flow_{'adjoint' if kern == 'adjoint' else 'step'} D3Q19 {args.storage}",
                 "workload": f"pipe bend {args.roof_n}^3 ({nb} nodes, {byts/1e9:.2f} GB algorithmic per launch)",
                 "bytes_per_node": (ADJ_BYTES if kern == "adjoint" else FWD_BYTES)[args.storage],

@@ -500,7 +500,9 @@ struct AdjMinBlocks {
         (L::Q == 19 && sizeof(R) == 4 && !REDUCE) ? (THERMAL ? 5 : 6) : 1;
 };
 
-template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
+// THERMAL: the coupling field is present; CPL_RT: decide at run time from
+// whether a coupling field is given (one code path for mixed batches)
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL, bool CPL_RT = false>
 __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
     R s[L::Q];
     pull_adjoint<L>(a, c, s);
@@ -526,7 +528,7 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
         const R om = a.omega;
         const R base = om * m.A - (type == VEL ? a.src_in : R(0));
         R v0 = 0, v1 = 0, v2 = 0;
-        if (THERMAL) {
+        if (THERMAL || (CPL_RT && a.cpl != nullptr)) {
             v0 = a.cpl[c.n];
             v1 = a.cpl[a.np + c.n];
             v2 = a.cpl[2 * a.np + c.n];
@@ -873,128 +875,82 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
 // resident lattice in a phase.  A tile is one block of that lattice's own
 // single-lattice launch geometry (same threads, same warps), so each lattice's
 // arithmetic and partial sums are bit-identical to its single-lattice solve,
-// whatever else is resident.
+// whatever else is resident.  Each lattice's argument blocks live in
+// __constant__ memory, one per step parity (buffers swapped), so the node code
+// reads its arguments from the constant cache exactly as the single-lattice
+// kernels read theirs from the parameter bank.
 // ---------------------------------------------------------------------------
+constexpr int kBatchSlots = 32;
+
 template <typename T, typename TG, typename TA, typename R>
-struct BatchSlot {
-    FlowArgs<T, TA, R> f;
-    ThermArgs<TG, TA, R> t;
-    void* buf[4][2];   // per phase (flow, temperature, adjoint, temperature adjoint)
-    int cur[4];        // per phase: buffer read at step 0 of a graph block
-    int gx, gy, bx, by;
+struct BatchConst {
+    FlowArgs<T, TA, R> f[kBatchSlots][2];   // [slot][parity]: flow and flow-adjoint buffers
+    ThermArgs<TG, TA, R> t[kBatchSlots][2]; // [slot][parity]: temperature and its adjoint
+    int4 geom[kBatchSlots];                 // log2(block x), block y, blocks (partials), unused
+    int cur[kBatchSlots];                   // parity of step 0 of a graph block
+    int phase[kBatchSlots];                 // 0 flow, 1 temperature, 2 flow adjoint, 3 temperature adjoint
 };
 
-__device__ __forceinline__ Cell tile_cell(long long b, int gx, int gy, int bx, int by, int nx, int ny) {
-    const int tid = threadIdx.x;
-    const long long gxy = (long long)gx * gy;
-    const int z = (int)(b / gxy);
-    const int r = (int)(b - (long long)z * gxy);
-    const int tyb = r / gx, txb = r - tyb * gx;
-    Cell c;
-    c.x = txb * bx + (tid % bx);
-    c.y = tyb * by + (tid / bx);
-    c.z = z;
-    c.active = (tid < bx * by) && (c.x < nx) && (c.y < ny);
-    c.n = c.x + (long long)nx * (c.y + (long long)ny * c.z);
-    return c;
-}
-
-template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE>
-__global__ void __launch_bounds__(256) k_batch_flow(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
-                                                    const int2* __restrict__ tiles,
-                                                    const int* __restrict__ ntiles, int step) {
+// one persistent launch per step covers the tiles of every resident lattice,
+// each tile dispatching on its lattice's phase (uniform within a block):
+// 0 flow, 1 temperature, 2 flow adjoint, 3 temperature adjoint.  A tile entry
+// is (slot | z << 8, x0, y0, block id), so no division is needed.
+template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE, class Bank>
+__global__ void __launch_bounds__(256, 5)
+    k_batch(const int4* __restrict__ tiles, const int* __restrict__ ntiles, int step) {
+    const BatchConst<T, TG, TA, R>& C = Bank::get();
+    pdl_launch_dependents();
+    pdl_wait();
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tl = tiles[t];
-        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
-        FlowArgs<T, TA, R> a = S.f;
-        const int p = (S.cur[0] + step) & 1;
-        a.fin = (const T*)S.buf[0][p];
-        a.fout = (T*)S.buf[0][p ^ 1];
-        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
-        double acc[2] = {0.0, 0.0};
-        if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
-        if (REDUCE) block_partials<2>(acc, a.partials, tl.y);
-    }
-}
-
-// each slot takes the thermal-coupling variant only if it has a coupling field
-template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE>
-__global__ void __launch_bounds__(256) k_batch_adjoint(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
-                                                       const int2* __restrict__ tiles,
-                                                       const int* __restrict__ ntiles, int step) {
-    const int nt = *ntiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tl = tiles[t];
-        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
-        FlowArgs<T, TA, R> a = S.f;
-        const int p = (S.cur[2] + step) & 1;
-        a.ain = (const TA*)S.buf[2][p];
-        a.aout = (TA*)S.buf[2][p ^ 1];
-        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
-        double acc[1] = {0.0};
-        if (c.active) {
-            if (a.cpl)
-                flow_adjoint_node<L, T, TA, R, REDUCE, true>(a, c, acc);
-            else
-                flow_adjoint_node<L, T, TA, R, REDUCE, false>(a, c, acc);
+        const int4 tl = tiles[t];
+        const int sl = tl.x & 0xff;
+        const int par = (C.cur[sl] + step) & 1;
+        const int4 g = C.geom[sl];
+        const int P = C.phase[sl];
+        Cell c;
+        const int tid = threadIdx.x;
+        c.x = tl.y + (tid & ((1 << g.x) - 1));
+        c.y = tl.z + (tid >> g.x);
+        c.z = tl.x >> 8;
+        const bool in_tile = tid < (g.y << g.x);
+        if (P == 0 || P == 2) {
+            const FlowArgs<T, TA, R>& a = C.f[sl][par];
+            c.active = in_tile && c.x < a.nx && c.y < a.ny;
+            c.n = c.x + (long long)a.nx * (c.y + (long long)a.ny * c.z);
+            if (P == 0) {
+                double acc[2] = {0.0, 0.0};
+                if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
+                if (REDUCE) block_partials<2>(acc, a.partials, tl.w);
+            } else {
+                double acc[1] = {0.0};
+                if (c.active) flow_adjoint_node<L, T, TA, R, REDUCE, false, true>(a, c, acc);
+                if (REDUCE) block_partials<1>(acc, a.partials, tl.w);
+            }
+        } else {
+            const ThermArgs<TG, TA, R>& a = C.t[sl][par];
+            c.active = in_tile && c.x < a.nx && c.y < a.ny;
+            c.n = c.x + (long long)a.nx * (c.y + (long long)a.ny * c.z);
+            double acc[1] = {0.0};
+            if (P == 1) {
+                if (c.active) thermal_step_node<TG, TA, R, REDUCE>(a, c, acc);
+            } else {
+                if (c.active) thermal_adjoint_node<TG, TA, R, REDUCE>(a, c, acc);
+            }
+            if (REDUCE) block_partials<1>(acc, a.partials, tl.w);
         }
-        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
-    }
-}
-
-template <typename T, typename TG, typename TA, typename R, bool REDUCE>
-__global__ void __launch_bounds__(256) k_batch_thermal(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
-                                                       const int2* __restrict__ tiles,
-                                                       const int* __restrict__ ntiles, int step) {
-    const int nt = *ntiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tl = tiles[t];
-        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
-        ThermArgs<TG, TA, R> a = S.t;
-        const int p = (S.cur[1] + step) & 1;
-        a.gin = (const TG*)S.buf[1][p];
-        a.gout = (TG*)S.buf[1][p ^ 1];
-        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
-        double acc[1] = {0.0};
-        if (c.active) thermal_step_node<TG, TA, R, REDUCE>(a, c, acc);
-        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
-    }
-}
-
-template <typename T, typename TG, typename TA, typename R, bool REDUCE>
-__global__ void __launch_bounds__(256) k_batch_thermal_adjoint(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
-                                                               const int2* __restrict__ tiles,
-                                                               const int* __restrict__ ntiles, int step) {
-    const int nt = *ntiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tl = tiles[t];
-        const BatchSlot<T, TG, TA, R>& S = slots[tl.x];
-        ThermArgs<TG, TA, R> a = S.t;
-        const int p = (S.cur[3] + step) & 1;
-        a.ain = (const TA*)S.buf[3][p];
-        a.aout = (TA*)S.buf[3][p ^ 1];
-        const Cell c = tile_cell(tl.y, S.gx, S.gy, S.bx, S.by, a.nx, a.ny);
-        double acc[1] = {0.0};
-        if (c.active) thermal_adjoint_node<TG, TA, R, REDUCE>(a, c, acc);
-        if (REDUCE) block_partials<1>(acc, a.partials, tl.y);
     }
 }
 
 // per-lattice second stage of the batched reductions: one block per listed
 // slot sums that slot's partials in the same fixed order as k_finalize
-template <int NV, typename T, typename TG, typename TA, typename R>
-__global__ void __launch_bounds__(256) k_batch_finalize(const BatchSlot<T, TG, TA, R>* __restrict__ slots,
-                                                        const int* __restrict__ list,
-                                                        const int* __restrict__ nlist,
-                                                        double* __restrict__ results) {
-    const int n = *nlist;
+template <int NV, typename T, typename TG, typename TA, typename R, class Bank>
+__device__ __forceinline__ void batch_finalize_slot(const BatchConst<T, TG, TA, R>& C, int slot,
+                                                    double* __restrict__ results) {
     __shared__ double sh[NV][8];
-    for (int q = blockIdx.x; q < n; q += gridDim.x) {
-        const int slot = list[q];
-        const BatchSlot<T, TG, TA, R>& S = slots[slot];
-        const double* __restrict__ partials = S.f.partials;
-        const long long nblocks = (long long)S.gx * S.gy * S.f.nz;
+    {
+        const double* __restrict__ partials = C.f[slot][0].partials;
+        const long long nblocks = C.geom[slot].z;
         double s[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] = 0.0;
@@ -1018,6 +974,22 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const BatchSlot<T, TG, T
             }
         }
         __syncthreads();
+    }
+}
+
+// the flow phase sums two values (|u| and inlet rho), the others one
+template <typename T, typename TG, typename TA, typename R, class Bank>
+__global__ void __launch_bounds__(256) k_batch_finalize(const int* __restrict__ list,
+                                                        const int* __restrict__ nlist,
+                                                        double* __restrict__ results) {
+    const BatchConst<T, TG, TA, R>& C = Bank::get();
+    const int n = *nlist;
+    for (int q = blockIdx.x; q < n; q += gridDim.x) {
+        const int slot = list[q];
+        if (C.phase[slot] == 0)
+            batch_finalize_slot<2, T, TG, TA, R, Bank>(C, slot, results);
+        else
+            batch_finalize_slot<1, T, TG, TA, R, Bank>(C, slot, results);
     }
 }
 

@@ -82,15 +82,21 @@ cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, d
 cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64, long long n,
                            cudaStream_t s);
 
-// batched (serving) kernels, D3Q19, storage 1-3.  phase: 0 flow, 1 temperature,
-// 2 flow adjoint, 3 temperature adjoint
-size_t batch_slot_bytes(int storage);
-void batch_fill_slot(int storage, void* dst, const FlowLaunch& f, const ThermLaunch& t,
-                     void* const bufs[4][2], const int cur[4], int gx, int gy, int bx, int by);
-cudaError_t batch_launch(int storage, int phase, bool reduce, bool thermal, const void* slots,
-                         const int2* tiles, const int* ntiles, int step, int grid, cudaStream_t s);
-cudaError_t batch_finalize_launch(int storage, int nv, const void* slots, const int* list,
-                                  const int* nlist, double* results, int grid, cudaStream_t s);
+// batched (serving) kernels, D3Q19, storage 1-3: one launch per step over the
+// tiles of all resident lattices (each in its own phase: 0 flow,
+// 1 temperature, 2 flow adjoint, 3 temperature adjoint).  The lattices'
+// arguments sit in a __constant__ bank per storage type, filled on the host.
+size_t batch_bank_bytes(int storage);
+int batch_max_slots();
+int batch_blocks_per_sm(int storage);
+void batch_fill_slot(int storage, void* bank, int slot, const FlowLaunch& f, const ThermLaunch& t,
+                     void* const bufs[4][2], int cur_flow_or_adj, int cur_therm, int phase,
+                     int gx, int gy, int bx, int by);
+cudaError_t batch_upload_bank(int storage, const void* bank, cudaStream_t s);
+cudaError_t batch_launch(int storage, bool reduce, const int4* tiles, const int* ntiles, int step,
+                         int grid, cudaStream_t s);
+cudaError_t batch_finalize_launch(int storage, const int* list, const int* nlist, double* results,
+                                  int grid, cudaStream_t s);
 
 // record an error message for lbm_last_error() and return the status
 int set_error(int status, const char* msg);

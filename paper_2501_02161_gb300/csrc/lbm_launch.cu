@@ -1,5 +1,6 @@
 // lbm_launch.cu -- template instantiation and dispatch of the kernels for each
 // (stencil, storage) pair.
+#include <algorithm>
 #include <cstring>
 
 #include "lbm_device.cuh"
@@ -221,112 +222,167 @@ cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64,
 }
 
 // ---------------------------------------------------------------------------
-// batched (serving) kernels: D3Q19 with FP32 arithmetic (storage 1, 2, 3)
+// batched (serving) kernels: D3Q19 with FP32 arithmetic (storage 1, 2, 3).
+// One __constant__ bank per storage type holds the resident lattices'
+// argument blocks; one batch per storage type may be live at a time.
 // ---------------------------------------------------------------------------
 namespace {
 template <int S>
-using SlotT = BatchSlot<typename StorageTypes<S>::T, typename StorageTypes<S>::TG,
-                        typename StorageTypes<S>::TA, typename StorageTypes<S>::R>;
+using BankT = BatchConst<typename StorageTypes<S>::T, typename StorageTypes<S>::TG,
+                         typename StorageTypes<S>::TA, typename StorageTypes<S>::R>;
 
-template <int S>
-void fill_slot(void* dst, const FlowLaunch& f, const ThermLaunch& t, void* const bufs[4][2],
-               const int cur[4], int gx, int gy, int bx, int by) {
-    SlotT<S> sl;
-    std::memset(&sl, 0, sizeof(sl));
-    sl.f = flow_args<S>(f);
-    sl.t = therm_args<S>(t);
-    for (int p = 0; p < 4; ++p) {
-        sl.buf[p][0] = bufs[p][0];
-        sl.buf[p][1] = bufs[p][1];
-        sl.cur[p] = cur[p];
-    }
-    sl.gx = gx;
-    sl.gy = gy;
-    sl.bx = bx;
-    sl.by = by;
-    std::memcpy(dst, &sl, sizeof(sl));
+__constant__ BankT<1> c_bank1;
+__constant__ BankT<2> c_bank2;
+__constant__ BankT<3> c_bank3;
+
+template <int S> struct Bank;
+template <> struct Bank<1> { __device__ __forceinline__ static const BankT<1>& get() { return c_bank1; } };
+template <> struct Bank<2> { __device__ __forceinline__ static const BankT<2>& get() { return c_bank2; } };
+template <> struct Bank<3> { __device__ __forceinline__ static const BankT<3>& get() { return c_bank3; } };
+
+template <typename... Args>
+void launch_pdl_grid(void (*kernel)(Args...), int grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <int S>
-void batch_dispatch(int phase, bool reduce, bool thermal, const void* slots, const int2* tiles,
-                    const int* ntiles, int step, int grid, cudaStream_t s) {
+void batch_dispatch(bool reduce, const int4* tiles, const int* ntiles, int step, int grid,
+                    cudaStream_t s) {
     using T = typename StorageTypes<S>::T;
     using TG = typename StorageTypes<S>::TG;
     using TA = typename StorageTypes<S>::TA;
     using R = typename StorageTypes<S>::R;
-    const SlotT<S>* sl = (const SlotT<S>*)slots;
-    switch (phase) {
-        case 0:
-            if (reduce) k_batch_flow<D3Q19, T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            else k_batch_flow<D3Q19, T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            break;
-        case 1:
-            if (reduce) k_batch_thermal<T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            else k_batch_thermal<T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            break;
-        case 2:
-            (void)thermal;
-            if (reduce) k_batch_adjoint<D3Q19, T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            else k_batch_adjoint<D3Q19, T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            break;
-        default:
-            if (reduce) k_batch_thermal_adjoint<T, TG, TA, R, true><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            else k_batch_thermal_adjoint<T, TG, TA, R, false><<<grid, 256, 0, s>>>(sl, tiles, ntiles, step);
-            break;
-    }
-}
-
-template <int S>
-void batch_finalize_dispatch(int nv, const void* slots, const int* list, const int* nlist,
-                             double* results, int grid, cudaStream_t s) {
-    using T = typename StorageTypes<S>::T;
-    using TG = typename StorageTypes<S>::TG;
-    using TA = typename StorageTypes<S>::TA;
-    using R = typename StorageTypes<S>::R;
-    const SlotT<S>* sl = (const SlotT<S>*)slots;
-    if (nv == 2)
-        k_batch_finalize<2, T, TG, TA, R><<<grid, 256, 0, s>>>(sl, list, nlist, results);
+    if (reduce)
+        launch_pdl_grid(k_batch<D3Q19, T, TG, TA, R, true, Bank<S>>, grid, s, tiles, ntiles, step);
     else
-        k_batch_finalize<1, T, TG, TA, R><<<grid, 256, 0, s>>>(sl, list, nlist, results);
+        launch_pdl_grid(k_batch<D3Q19, T, TG, TA, R, false, Bank<S>>, grid, s, tiles, ntiles, step);
+}
+
+template <int S>
+void batch_finalize_dispatch(const int* list, const int* nlist, double* results, int grid,
+                             cudaStream_t s) {
+    using T = typename StorageTypes<S>::T;
+    using TG = typename StorageTypes<S>::TG;
+    using TA = typename StorageTypes<S>::TA;
+    using R = typename StorageTypes<S>::R;
+    k_batch_finalize<T, TG, TA, R, Bank<S>><<<grid, 256, 0, s>>>(list, nlist, results);
+}
+
+template <int S>
+void fill(void* dst, int slot, const FlowLaunch& f, const ThermLaunch& t, void* const bufs[4][2],
+          int cur_flow_or_adj, int cur_therm, int phase_flow, int phase_therm, int gx, int gy, int bx, int by) {
+    BankT<S>* bank = (BankT<S>*)dst;
+    for (int p = 0; p < 2; ++p) {
+        FlowLaunch fl = f;
+        ThermLaunch tl = t;
+        const int pf = (cur_flow_or_adj + p) & 1, pt = (cur_therm + p) & 1;
+        // the lattice's current phase decides which pair the parity swaps
+        fl.fin = bufs[0][phase_flow == 0 ? pf : 0];
+        fl.fout = bufs[0][phase_flow == 0 ? pf ^ 1 : 1];
+        fl.ain = bufs[2][phase_flow == 2 ? pf : 0];
+        fl.aout = bufs[2][phase_flow == 2 ? pf ^ 1 : 1];
+        tl.gin = bufs[1][phase_therm == 1 ? pt : 0];
+        tl.gout = bufs[1][phase_therm == 1 ? pt ^ 1 : 1];
+        tl.ain = bufs[3][phase_therm == 3 ? pt : 0];
+        tl.aout = bufs[3][phase_therm == 3 ? pt ^ 1 : 1];
+        bank->f[slot][p] = flow_args<S>(fl);
+        bank->t[slot][p] = therm_args<S>(tl);
+    }
+    int lg = 0;
+    while ((1 << lg) < bx) ++lg;  // block widths are 32, 64 or 128
+    bank->geom[slot] = make_int4(lg, by, gx * gy * f.nz, 0);
+    bank->cur[slot] = 0;
+    bank->phase[slot] = phase_flow >= 0 ? phase_flow : phase_therm;
 }
 }  // namespace
 
-size_t batch_slot_bytes(int storage) {
+size_t batch_bank_bytes(int storage) {
     switch (storage) {
-        case 1: return sizeof(SlotT<1>);
-        case 2: return sizeof(SlotT<2>);
-        case 3: return sizeof(SlotT<3>);
+        case 1: return sizeof(BankT<1>);
+        case 2: return sizeof(BankT<2>);
+        case 3: return sizeof(BankT<3>);
         default: return 0;
     }
 }
 
-void batch_fill_slot(int storage, void* dst, const FlowLaunch& f, const ThermLaunch& t,
-                     void* const bufs[4][2], const int cur[4], int gx, int gy, int bx, int by) {
+int batch_max_slots() { return kBatchSlots; }
+
+void batch_fill_slot(int storage, void* bank, int slot, const FlowLaunch& f, const ThermLaunch& t,
+                     void* const bufs[4][2], int cur_flow_or_adj, int cur_therm, int phase,
+                     int gx, int gy, int bx, int by) {
+    const int pf = (phase == 0 || phase == 2) ? phase : -1;
+    const int pt = (phase == 1 || phase == 3) ? phase : -1;
     switch (storage) {
-        case 1: fill_slot<1>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
-        case 2: fill_slot<2>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
-        case 3: fill_slot<3>(dst, f, t, bufs, cur, gx, gy, bx, by); break;
+        case 1: fill<1>(bank, slot, f, t, bufs, cur_flow_or_adj, cur_therm, pf, pt, gx, gy, bx, by); break;
+        case 2: fill<2>(bank, slot, f, t, bufs, cur_flow_or_adj, cur_therm, pf, pt, gx, gy, bx, by); break;
+        case 3: fill<3>(bank, slot, f, t, bufs, cur_flow_or_adj, cur_therm, pf, pt, gx, gy, bx, by); break;
         default: break;
     }
 }
 
-cudaError_t batch_launch(int storage, int phase, bool reduce, bool thermal, const void* slots,
-                         const int2* tiles, const int* ntiles, int step, int grid, cudaStream_t s) {
+cudaError_t batch_upload_bank(int storage, const void* bank, cudaStream_t s) {
     switch (storage) {
-        case 1: batch_dispatch<1>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
-        case 2: batch_dispatch<2>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
-        case 3: batch_dispatch<3>(phase, reduce, thermal, slots, tiles, ntiles, step, grid, s); break;
+        case 1: return cudaMemcpyToSymbolAsync(c_bank1, bank, sizeof(BankT<1>), 0, cudaMemcpyHostToDevice, s);
+        case 2: return cudaMemcpyToSymbolAsync(c_bank2, bank, sizeof(BankT<2>), 0, cudaMemcpyHostToDevice, s);
+        case 3: return cudaMemcpyToSymbolAsync(c_bank3, bank, sizeof(BankT<3>), 0, cudaMemcpyHostToDevice, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batch_blocks_per_sm(int storage) {
+    auto occ = [](const void* k) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, 0);
+        return n;
+    };
+    int m = 0;
+    switch (storage) {
+        case 1: {
+            using T = StorageTypes<1>::T; using TG = StorageTypes<1>::TG; using TA = StorageTypes<1>::TA; using R = StorageTypes<1>::R;
+            m = occ((const void*)k_batch<D3Q19, T, TG, TA, R, false, Bank<1>>);
+            break;
+        }
+        case 2: {
+            using T = StorageTypes<2>::T; using TG = StorageTypes<2>::TG; using TA = StorageTypes<2>::TA; using R = StorageTypes<2>::R;
+            m = occ((const void*)k_batch<D3Q19, T, TG, TA, R, false, Bank<2>>);
+            break;
+        }
+        case 3: {
+            using T = StorageTypes<3>::T; using TG = StorageTypes<3>::TG; using TA = StorageTypes<3>::TA; using R = StorageTypes<3>::R;
+            m = occ((const void*)k_batch<D3Q19, T, TG, TA, R, false, Bank<3>>);
+            break;
+        }
+        default: break;
+    }
+    return m > 0 ? m : 4;
+}
+
+cudaError_t batch_launch(int storage, bool reduce, const int4* tiles, const int* ntiles, int step,
+                         int grid, cudaStream_t s) {
+    switch (storage) {
+        case 1: batch_dispatch<1>(reduce, tiles, ntiles, step, grid, s); break;
+        case 2: batch_dispatch<2>(reduce, tiles, ntiles, step, grid, s); break;
+        case 3: batch_dispatch<3>(reduce, tiles, ntiles, step, grid, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t batch_finalize_launch(int storage, int nv, const void* slots, const int* list,
-                                  const int* nlist, double* results, int grid, cudaStream_t s) {
+cudaError_t batch_finalize_launch(int storage, const int* list, const int* nlist, double* results,
+                                  int grid, cudaStream_t s) {
     switch (storage) {
-        case 1: batch_finalize_dispatch<1>(nv, slots, list, nlist, results, grid, s); break;
-        case 2: batch_finalize_dispatch<2>(nv, slots, list, nlist, results, grid, s); break;
-        case 3: batch_finalize_dispatch<3>(nv, slots, list, nlist, results, grid, s); break;
+        case 1: batch_finalize_dispatch<1>(list, nlist, results, grid, s); break;
+        case 2: batch_finalize_dispatch<2>(list, nlist, results, grid, s); break;
+        case 3: batch_finalize_dispatch<3>(list, nlist, results, grid, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -810,26 +810,24 @@ struct lbm_batch {
     int K = 1000;
     int max_slots = 0;
     int grid = 0;
-    size_t slot_bytes = 0;
     cudaStream_t stream = nullptr;
-    void* d_slots = nullptr;
-    std::vector<char> h_slots;
-    int2* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<char> h_bank;   // host image of the __constant__ argument bank
+    int4* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     long long tile_cap[4] = {0, 0, 0, 0};
-    int* d_lists = nullptr;  // 4 phase lists of max_slots slot ids
-    int* d_counts = nullptr; // ntiles[4], nslots[4]
+    int* d_lists = nullptr;  // resident slot ids
+    int* d_counts = nullptr; // tile count, slot count
     double* d_results = nullptr;
     double* h_results = nullptr;
     std::vector<BatchEntry> e;
     std::vector<std::pair<int, lbm_report>> done;
     bool dirty = true;
-    bool any_thermal = false;
-    std::map<std::pair<int, bool>, cudaGraphExec_t> graphs;
+    std::map<int, cudaGraphExec_t> graphs;
 };
 
 namespace {
 
-lbm_status batch_fail(lbm_status s, const std::string& m) { return fail(s, m); }
+// the __constant__ bank of a storage type serves one live batch at a time
+bool g_bank_busy[4] = {false, false, false, false};
 
 void batch_slot_refresh(lbm_batch* b, int i) {
     BatchEntry& en = b->e[i];
@@ -841,47 +839,49 @@ void batch_slot_refresh(lbm_batch* b, int i) {
     t.out0 = c->T;
     t.out1 = c->gpost;
     void* bufs[4][2] = {{c->f[0], c->f[1]}, {c->g[0], c->g[1]}, {c->fa[0], c->fa[1]}, {c->ga[0], c->ga[1]}};
-    int cur[4] = {c->fcur, c->gcur, c->facur, c->gacur};
-    batch_fill_slot(b->storage, b->h_slots.data() + (size_t)i * b->slot_bytes, f, t, bufs, cur,
+    const int ph = en.phase;
+    const int cur_fa = ph == SP_ADJ ? c->facur : c->fcur;
+    const int cur_th = ph == SP_TADJ ? c->gacur : c->gcur;
+    batch_fill_slot(b->storage, b->h_bank.data(), i, f, t, bufs, cur_fa, cur_th, ph,
                     (int)c->geom.grid.x, (int)c->geom.grid.y, (int)c->geom.block.x, (int)c->geom.block.y);
 }
 
-// rebuild slot descriptors, per-phase tile tables and slot lists on the device
+// rebuild the argument bank, the tile table and the slot list on the device
 lbm_status batch_upload(lbm_batch* b) {
-    std::vector<std::vector<int2>> tiles(4);
-    std::vector<int> lists(4 * (size_t)b->max_slots, 0);
-    int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    b->any_thermal = false;
+    std::vector<int4> tiles;
+    std::vector<int> list;
     for (int i = 0; i < b->max_slots; ++i) {
         BatchEntry& en = b->e[i];
         if (!en.used || en.phase == SP_DONE) continue;
         batch_slot_refresh(b, i);
-        const int ph = en.phase;
-        const long long nb = en.ctx->geom.nblocks;
-        for (long long k = 0; k < nb; ++k) tiles[ph].push_back(make_int2(i, (int)k));
-        lists[(size_t)ph * b->max_slots + counts[4 + ph]++] = i;
-        if (ph == SP_ADJ && en.ctx->thermal) b->any_thermal = true;
+        const Geom& g = en.ctx->geom;
+        // the single-lattice launch's blocks, in its block-id order
+        for (unsigned z = 0; z < g.grid.z; ++z)
+            for (unsigned by = 0; by < g.grid.y; ++by)
+                for (unsigned bx = 0; bx < g.grid.x; ++bx) {
+                    const int bid = (int)(bx + g.grid.x * (by + g.grid.y * z));
+                    tiles.push_back(make_int4(i | (int)(z << 8), (int)(bx * g.block.x),
+                                              (int)(by * g.block.y), bid));
+                }
+        list.push_back(i);
     }
-    for (int ph = 0; ph < 4; ++ph) {
-        counts[ph] = (int)tiles[ph].size();
-        if ((long long)tiles[ph].size() > b->tile_cap[ph]) {
-            if (b->d_tiles[ph]) CUDA_TRY(cudaFree(b->d_tiles[ph]));
-            b->d_tiles[ph] = nullptr;
-            long long cap = std::max<long long>(1024, (long long)tiles[ph].size() * 2);
-            CUDA_TRY(cudaMalloc(&b->d_tiles[ph], sizeof(int2) * cap));
-            b->tile_cap[ph] = cap;
-            // the graphs hold the old table pointers
-            for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-            b->graphs.clear();
-        }
-        if (!tiles[ph].empty())
-            CUDA_TRY(cudaMemcpyAsync(b->d_tiles[ph], tiles[ph].data(), sizeof(int2) * tiles[ph].size(),
-                                     cudaMemcpyHostToDevice, b->stream));
+    int counts[2] = {(int)tiles.size(), (int)list.size()};
+    if ((long long)tiles.size() > b->tile_cap[0]) {
+        if (b->d_tiles[0]) CUDA_TRY(cudaFree(b->d_tiles[0]));
+        b->d_tiles[0] = nullptr;
+        long long cap = std::max<long long>(1024, (long long)tiles.size() * 2);
+        CUDA_TRY(cudaMalloc(&b->d_tiles[0], sizeof(int4) * cap));
+        b->tile_cap[0] = cap;
+        for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old table
+        b->graphs.clear();
     }
-    CUDA_TRY(cudaMemcpyAsync(b->d_slots, b->h_slots.data(), b->slot_bytes * b->max_slots,
-                             cudaMemcpyHostToDevice, b->stream));
-    CUDA_TRY(cudaMemcpyAsync(b->d_lists, lists.data(), sizeof(int) * lists.size(),
-                             cudaMemcpyHostToDevice, b->stream));
+    if (!tiles.empty())
+        CUDA_TRY(cudaMemcpyAsync(b->d_tiles[0], tiles.data(), sizeof(int4) * tiles.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(batch_upload_bank(b->storage, b->h_bank.data(), b->stream));
+    if (!list.empty())
+        CUDA_TRY(cudaMemcpyAsync(b->d_lists, list.data(), sizeof(int) * list.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
     CUDA_TRY(cudaMemcpyAsync(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, b->stream));
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->dirty = false;
@@ -895,18 +895,13 @@ int batch_mask(lbm_batch* b) {
     return m;
 }
 
-cudaError_t batch_enqueue(lbm_batch* b, int mask, bool thermal_adj) {
+cudaError_t batch_enqueue(lbm_batch* b) {
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < b->K && e == cudaSuccess; ++s)
-        for (int ph = 0; ph < 4 && e == cudaSuccess; ++ph)
-            if (mask & (1 << ph))
-                e = batch_launch(b->storage, ph, s == b->K - 1, ph == SP_ADJ && thermal_adj, b->d_slots,
-                                 b->d_tiles[ph], b->d_counts + ph, s, b->grid, b->stream);
-    for (int ph = 0; ph < 4 && e == cudaSuccess; ++ph)
-        if (mask & (1 << ph))
-            e = batch_finalize_launch(b->storage, ph == SP_FLOW ? 2 : 1, b->d_slots,
-                                      b->d_lists + (size_t)ph * b->max_slots, b->d_counts + 4 + ph,
-                                      b->d_results, b->grid, b->stream);
+        e = batch_launch(b->storage, s == b->K - 1, b->d_tiles[0], b->d_counts, s, b->grid, b->stream);
+    if (e == cudaSuccess)
+        e = batch_finalize_launch(b->storage, b->d_lists, b->d_counts + 1, b->d_results, b->grid,
+                                  b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * 2 * b->max_slots,
                             cudaMemcpyDeviceToHost, b->stream);
@@ -997,21 +992,23 @@ lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int m
     if (storage == LBM_FP64) return fail(LBM_ERR_UNSUPPORTED, "batches are built for FP32 arithmetic storage");
     if (storage < LBM_FP32 || storage > LBM_BF16_OFS) return fail(LBM_ERR_ARG, "unknown storage");
     if (check_every <= 0 || (check_every & 1)) return fail(LBM_ERR_ARG, "check_every must be positive and even");
-    if (max_slots <= 0 || max_slots > 4096) return fail(LBM_ERR_ARG, "max_slots out of range");
+    if (max_slots <= 0 || max_slots > batch_max_slots())
+        return fail(LBM_ERR_ARG, "max_slots must be in [1, " + std::to_string(batch_max_slots()) + "]");
+    if (g_bank_busy[storage])
+        return fail(LBM_ERR_ARG, "a batch of this storage type is already live in this process");
     lbm_batch* b = new lbm_batch();
     cudaGetDevice(&b->device);
     b->storage = storage;
     b->K = check_every;
     b->max_slots = max_slots;
-    b->slot_bytes = batch_slot_bytes(storage);
-    b->h_slots.assign(b->slot_bytes * max_slots, 0);
+    b->h_bank.assign(batch_bank_bytes(storage), 0);
     b->e.resize(max_slots);
+    g_bank_busy[storage] = true;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    b->grid = std::max(1, sms) * 4;
+    b->grid = std::max(1, sms) * batch_blocks_per_sm(storage);
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, b->slot_bytes * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_lists, sizeof(int) * 4 * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_lists, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 8);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_results, sizeof(double) * 2 * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_results, sizeof(double) * 2 * max_slots);
@@ -1031,7 +1028,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     for (int ph = 0; ph < 4; ++ph)
         if (b->d_tiles[ph]) cudaFree(b->d_tiles[ph]);
-    if (b->d_slots) cudaFree(b->d_slots);
+    g_bank_busy[b->storage] = false;
     if (b->d_lists) cudaFree(b->d_lists);
     if (b->d_counts) cudaFree(b->d_counts);
     if (b->d_results) cudaFree(b->d_results);
@@ -1092,12 +1089,12 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
     }
     const int mask = batch_mask(b);
     if (mask) {
-        auto key = std::make_pair(mask, b->any_thermal);
+        const int key = 0;  // one graph: the tables it reads live in device memory
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = batch_enqueue(b, mask, b->any_thermal);
+            cudaError_t e = batch_enqueue(b);
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);

@@ -108,7 +108,7 @@ def opt_step_gamma(lat, gamma: torch.Tensor, sens: torch.Tensor, step: float = 0
 class Batch:
     """Thin owner of an lbm_batch (same names as the C-ABI)."""
 
-    def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 64):
+    def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 32):
         self.lib = C.lib()
         self._b = ctypes.c_void_p()
         C.check(self.lib.lbm_batch_create(ctypes.byref(self._b), STORAGES[storage],
@@ -157,7 +157,7 @@ class Server:
     """Continuous-batching server over one GPU."""
 
     def __init__(self, storage: str = "fp32", budget_bytes: int | None = None,
-                 check_every: int = 500, max_slots: int = 64, tol: float = 1e-4,
+                 check_every: int = 500, max_slots: int = 32, tol: float = 1e-4,
                  max_steps: int = 20000, keep_designs: bool = True, device=None,
                  max_active_nodes: int = 6_000_000):
         self.device = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
