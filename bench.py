@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cap", type=int, default=CAP,
                    help="step cap per solve phase (lower it only for profiler launch lists)")
-    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve"],
+    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve", "batchcmp"],
                    help="kernels: time the fused step kernels on a --roof-n lattice; "
                         "precision: heat sink in FP64/FP32/FP16/BF16 storage, error per field; "
                         "autograd: the filtered / projected gradient loop")
@@ -209,6 +209,69 @@ def run_serve(args, nreq=None, device="cuda:0"):
     stable["online"] = run_all(make_requests(n, seed=5, rate=rate, re_range=(10.0, 80.0)), True)
     out["stable_re_10_80"] = stable
     return out
+
+
+def run_batchcmp(args):
+    """Throughput of the batched kernels against the single-context path on
+    the same lattices and step counts (forward + adjoint, fixed steps)."""
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.serve import Batch
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+
+    def single(lats, steps):
+        ss = [Solver.from_lattice(l, device="cuda:0") for l in lats]
+        for s in ss:
+            s.forward(tol=0, max_steps=1000, check_every=500)
+            s.adjoint(tol=0, max_steps=1000, check_every=500)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in ss:
+            s.forward(tol=0, max_steps=steps, check_every=500)
+            s.adjoint(tol=0, max_steps=steps, check_every=500)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for s in ss:
+            s.close()
+        return dt
+
+    def batched(lats, steps):
+        b = Batch("fp32", 500, 32)
+        ss = [Solver.from_lattice(l, device="cuda:0") for l in lats]
+        for s in ss:
+            b.admit(s, 0.0, 1000, True)
+        while b.step():
+            pass
+        b.poll()
+        for s in ss:
+            b.admit(s, 0.0, steps, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while b.step():
+            pass
+        dt = time.perf_counter() - t0
+        b.poll()
+        b.close()
+        for s in ss:
+            s.close()
+        return dt
+
+    cases = [("1 x 192x96x48", [I.pipe_bend_3d(n=192, ny=96, nz=48, width=12, re=20.0)], 4000),
+             ("1 x 64^3", [I.pipe_bend_3d(n=64, re=20.0)], 10000),
+             ("4 x 64^3", [I.pipe_bend_3d(n=64, re=20.0, seed=k) for k in range(4)], 4000),
+             ("16 x 32^3", [I.pipe_bend_3d(n=32, re=20.0, seed=k) for k in range(16)], 4000)]
+    out = {"mode": "batchcmp", "storage": "fp32", "steps": "forward N + adjoint N per lattice"}
+    for name, lats, steps in cases:
+        nodes = sum(l.n for l in lats)
+        ts, tb = single(lats, steps), batched(lats, steps)
+        out[name] = {"single_MLUPS": round(2 * nodes * steps / ts / 1e6, 1),
+                     "batched_MLUPS": round(2 * nodes * steps / tb / 1e6, 1)}
+    print(json.dumps(out))
 
 
 def run_kernels(args):
@@ -610,6 +673,8 @@ if __name__ == "__main__":
         run_precision(a)
     elif a.mode == "autograd":
         run_autograd(a)
+    elif a.mode == "batchcmp":
+        run_batchcmp(a)
     elif a.mode == "serve":
         import torch
         torch.cuda.set_device(0)
