@@ -34,6 +34,12 @@
 
 #define QMAX 19
 
+/* ORC_MUTATION plants one deliberate mistake (tests/test_oracle_mutations.py
+ * checks that the pins catch each); the normal build leaves it at 0. */
+#ifndef ORC_MUTATION
+#define ORC_MUTATION 0
+#endif
+
 enum { T_FLUID = 0, T_WALL = 1, T_VEL = 2, T_PRES = 3 };
 
 typedef struct {
@@ -181,7 +187,7 @@ static void equilibrium_jacobian(const lattice* L, const double u[3], double gam
             double d;
             if (model == 0) {
                 d = drho + rho0 * (3.0 * gamma * dot3(em, du) +
-                                   9.0 * gamma * gamma * emu * dot3(em, du) -
+                                   9.0 * gamma * (ORC_MUTATION == 5 ? 1.0 : gamma) * emu * dot3(em, du) -
                                    3.0 * gamma * gamma * dot3(u, du));
             } else {
                 d = drho + gamma * rho0 * (3.0 * dot3(em, du) + 9.0 * emu * dot3(em, du) -
@@ -286,7 +292,7 @@ static void bc_node(const lattice* L, const orc_problem* P, uint8_t fl, const do
         evec(L, i, e);
         double v = fs[L->opp[i]] + 6.0 * L->w[i] * P->rho0 * dot3(e, u);
         for (int a = 0; a < 3; a++)
-            if (n[a] == 0) v -= e[a] * N[a];
+            if (n[a] == 0) v -= (ORC_MUTATION == 1 ? -1.0 : 1.0) * e[a] * N[a];
         out[i] = v;
     }
 }
@@ -321,11 +327,11 @@ static void bc_jacobian(const lattice* L, const orc_problem* P, uint8_t fl,
             /* dN_t / d f_S,j = 1/2 e_j,t for e_j.n = 0 (u.t is fixed or zero) */
             if (dj == 0)
                 for (int a = 0; a < 3; a++)
-                    if (n[a] == 0) B[i][j] -= L->e[i][a] * 0.5 * L->e[j][a];
+                    if (n[a] == 0) B[i][j] -= L->e[i][a] * (ORC_MUTATION == 2 ? 1.0 : 0.5) * L->e[j][a];
             if (t == T_PRES) {
                 /* e_i.u = u_n (e_i.n) with u_n = (rho_out - K0 - 2 K-)/rho0 */
                 double dun = (dj == 0) ? -1.0 / P->rho0 : (dj < 0 ? -2.0 / P->rho0 : 0.0);
-                B[i][j] += 6.0 * L->w[i] * P->rho0 * di * dun;
+                B[i][j] += (ORC_MUTATION == 6 ? 3.0 : 6.0) * L->w[i] * P->rho0 * di * dun;
             }
         }
     }
@@ -448,7 +454,9 @@ static void adjoint_stream(const lattice* L, const orc_problem* P, const double*
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; n++)
         for (int i = 0; i < Q; i++)
-            fss[n * Q + i] = fs[neighbour(P, n, L->e[i][0], L->e[i][1], L->e[i][2]) * Q + i];
+            fss[n * Q + i] = (ORC_MUTATION == 4)
+                                 ? fs[neighbour(P, n, -L->e[i][0], -L->e[i][1], -L->e[i][2]) * Q + i]
+                                 : fs[neighbour(P, n, L->e[i][0], L->e[i][1], L->e[i][2]) * Q + i];
 }
 
 static long count_type(const orc_problem* P, const uint8_t* flags, int t) {
@@ -485,8 +493,8 @@ void orc_flow_adjoint_step(const orc_problem* P, const uint8_t* flags, const dou
         collision_jacobian(&L, P, flags[n], gamma[n], f + n * Q, C);
         for (int i = 0; i < Q; i++) {
             double s = 0;
-            for (int m = 0; m < Q; m++) s += C[m][i] * fss[n * Q + m]; /* C^T */
-            if (with_source && node_type(flags[n]) == T_VEL) s -= src;
+            for (int m = 0; m < Q; m++) s += (ORC_MUTATION == 3 ? C[i][m] : C[m][i]) * fss[n * Q + m]; /* C^T */
+            if (with_source && node_type(flags[n]) == T_VEL) s -= (ORC_MUTATION == 7 ? -src : src);
             if (coupling) s += coupling[n * Q + i];
             fsc_new[n * Q + i] = s;
         }
@@ -685,7 +693,7 @@ static void thermal_collision_jacobians(const lattice* LF, const lattice* LG,
         for (int i = 0; i < LF->Q; i++) {
             double du[3];
             for (int b = 0; b < 3; b++) du[b] = LF->e[i][b] / P->rho0;
-            Cf[k][i] = LG->w[k] * T * 4.0 * gamma * dot3(e, du) / tg;
+            Cf[k][i] = (ORC_MUTATION == 8 ? -1.0 : 1.0) * LG->w[k] * T * 4.0 * gamma * dot3(e, du) / tg;
         }
         Cgam[k] = -(g[k] - geq) * dinv + LG->w[k] * T * 4.0 * dot3(e, u) / tg;
     }

@@ -24,14 +24,16 @@ LIB = os.path.join(HERE, "liblbm_oracle.so")
 T_FLUID, T_WALL, T_VEL, T_PRES = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (OpenMP over nodes)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, target: str | None = None, mutation: int = 0) -> str:
+    """Compile the oracle with the host C compiler (OpenMP over nodes).
+    mutation > 0 builds a copy with one planted mistake into `target`."""
+    out = target or LIB
+    if force or mutation or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared",
-                               SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+                               f"-DORC_MUTATION={int(mutation)}", SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Problem(ctypes.Structure):
@@ -46,11 +48,24 @@ class Problem(ctypes.Structure):
 _lib = None
 
 
+def use_library(path: str | None):
+    """Load the oracle from `path` (None: the normal build) for later calls."""
+    global _lib
+    _lib = None
+    if path is not None:
+        _lib = _load(path)
+
+
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(LIB)
+        _lib = _load(build())
+    return _lib
+
+
+def _load(path: str):
+    if True:
+        L = ctypes.CDLL(path)
         P = ctypes.POINTER(Problem)
         d = ctypes.POINTER(ctypes.c_double)
         u8 = ctypes.POINTER(ctypes.c_uint8)
@@ -89,8 +104,7 @@ def lib():
         L.orc_objective.argtypes = [P, u8, d, d]
         L.orc_objective.restype = ctypes.c_double
         L.orc_lattice.restype = ctypes.c_int
-        _lib = L
-    return _lib
+        return L
 
 
 def _p(a, ctype=ctypes.c_double):
