@@ -374,6 +374,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(total_ms: float, total_ups: float, device):
+    """Whole-job figures over replicas: the slowest rank's time and the sum of
+    the cell updates of all ranks (weak scaling, no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(total_ups)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -449,12 +461,7 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(total_ups)], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ups = float(u.item())
+        total_ms, total_ups = aggregate_ranks(total_ms, total_ups, dev)
     value = total_ups / (total_ms * 1e-3) / 1e6
 
     hbm, peak_kind = peaks()

@@ -294,9 +294,11 @@ class Server:
 
 def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_steps: int = 20000,
                      check_every: int = 500, realtime: bool = True, keep_designs: bool = True,
-                     device=None):
+                     device=None, max_designs: int | None = None):
     """Baseline: one request at a time, in arrival order, through the
-    single-context solver (plain path, same tolerance and step caps)."""
+    single-context solver (plain path, same tolerance and step caps).
+    Finished designs stay resident like the server's (max_designs: LRU cap,
+    None = no cap) so optimisation steps warm-start the same way."""
     dev = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
     designs = OrderedDict()
     results = []
@@ -338,9 +340,11 @@ def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_ste
         results.append(res)
         if keep_designs and rep_status >= 0:
             designs[req.design] = (s, lat, gamma, sens)
-            while len(designs) > 16:
+            designs.move_to_end(req.design)
+            while max_designs is not None and len(designs) > max_designs:
                 designs.popitem(last=False)[1][0].close()
         else:
+            designs.pop(req.design, None)  # the design's state is no longer usable
             s.close()
     for v in designs.values():
         v[0].close()
