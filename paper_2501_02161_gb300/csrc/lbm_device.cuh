@@ -93,32 +93,32 @@ struct D3Q7 {
 template <typename T> struct Pop;
 template <> struct Pop<double> {
     using R = double;
-    __device__ __forceinline__ static R ld(const double* __restrict__ p, size_t k, R) { return __ldg(p + k); }
-    __device__ __forceinline__ static void st(double* __restrict__ p, size_t k, R v, R) { p[k] = v; }
+    __device__ __forceinline__ static R ld(const double* __restrict__ p, long long k, R) { return __ldg(p + k); }
+    __device__ __forceinline__ static void st(double* __restrict__ p, long long k, R v, R) { p[k] = v; }
     __device__ __forceinline__ static double enc(R v, R) { return v; }
 };
 template <> struct Pop<float> {
     using R = float;
-    __device__ __forceinline__ static R ld(const float* __restrict__ p, size_t k, R) { return __ldg(p + k); }
-    __device__ __forceinline__ static void st(float* __restrict__ p, size_t k, R v, R) { p[k] = v; }
+    __device__ __forceinline__ static R ld(const float* __restrict__ p, long long k, R) { return __ldg(p + k); }
+    __device__ __forceinline__ static void st(float* __restrict__ p, long long k, R v, R) { p[k] = v; }
     __device__ __forceinline__ static float enc(R v, R) { return v; }
 };
 template <> struct Pop<__half> {
     using R = float;
-    __device__ __forceinline__ static R ld(const __half* __restrict__ p, size_t k, R off) {
+    __device__ __forceinline__ static R ld(const __half* __restrict__ p, long long k, R off) {
         return off + __half2float(__ldg(p + k));
     }
-    __device__ __forceinline__ static void st(__half* __restrict__ p, size_t k, R v, R off) {
+    __device__ __forceinline__ static void st(__half* __restrict__ p, long long k, R v, R off) {
         p[k] = __float2half_rn(v - off);
     }
     __device__ __forceinline__ static __half enc(R v, R off) { return __float2half_rn(v - off); }
 };
 template <> struct Pop<__nv_bfloat16> {
     using R = float;
-    __device__ __forceinline__ static R ld(const __nv_bfloat16* __restrict__ p, size_t k, R off) {
+    __device__ __forceinline__ static R ld(const __nv_bfloat16* __restrict__ p, long long k, R off) {
         return off + __bfloat162float(__ldg(p + k));
     }
-    __device__ __forceinline__ static void st(__nv_bfloat16* __restrict__ p, size_t k, R v, R off) {
+    __device__ __forceinline__ static void st(__nv_bfloat16* __restrict__ p, long long k, R v, R off) {
         p[k] = __float2bfloat16_rn(v - off);
     }
     __device__ __forceinline__ static __nv_bfloat16 enc(R v, R off) { return __float2bfloat16_rn(v - off); }
@@ -192,15 +192,31 @@ __device__ __forceinline__ Cell this_cell(int nx, int ny) {
     return c;
 }
 
-// node index of x + s*e_i with periodic wrap (s = +1 or -1)
+// offsets (in nodes) from a node to its six axis neighbours, periodic wrap
+// included; they fit in 32 bits because node counts stay below 2^31.  A pull
+// then costs one integer add per population instead of a wrapped 3-D index.
+struct Nbr {
+    int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Nbr neighbours(const Cell& c, int nx, int ny, int nz) {
+    const int sy = nx, sz = nx * ny;
+    Nbr o;
+    o.xm = c.x == 0 ? nx - 1 : -1;
+    o.xp = c.x == nx - 1 ? 1 - nx : 1;
+    o.ym = c.y == 0 ? (ny - 1) * sy : -sy;
+    o.yp = c.y == ny - 1 ? (1 - ny) * sy : sy;
+    o.zm = c.z == 0 ? (nz - 1) * sz : -sz;
+    o.zp = c.z == nz - 1 ? (1 - nz) * sz : sz;
+    return o;
+}
+
+// offset of x + s e_i (s = +1 or -1); the selections fold at compile time
 template <class L>
-__device__ __forceinline__ long long shifted(const Cell& c, int i, int s, int nx, int ny, int nz) {
-    int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
-    int x = c.x + dx, y = c.y + dy, z = c.z + dz;
-    x = x < 0 ? nx - 1 : (x >= nx ? 0 : x);
-    y = y < 0 ? ny - 1 : (y >= ny ? 0 : y);
-    z = z < 0 ? nz - 1 : (z >= nz ? 0 : z);
-    return x + (long long)nx * (y + (long long)ny * z);
+__device__ __forceinline__ int nbr_offset(const Nbr& o, int i, int s) {
+    const int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
+    return (dx < 0 ? o.xm : (dx > 0 ? o.xp : 0)) + (dy < 0 ? o.ym : (dy > 0 ? o.yp : 0)) +
+           (dz < 0 ? o.zm : (dz > 0 ? o.zp : 0));
 }
 
 // Programmatic dependent launch (sm_90+): a step kernel lets the next step's
@@ -353,11 +369,10 @@ __device__ __forceinline__ void bounce(R (&f)[L::Q]) {
 // pull the post-collision populations of the upstream neighbours and apply B
 template <class L, typename T, typename TA, typename R>
 __device__ __forceinline__ int pull_forward(const FlowArgs<T, TA, R>& a, const Cell& c, R (&f)[L::Q]) {
+    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+    const T* __restrict__ p = a.fin + c.n;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const long long src = shifted<L>(c, i, -1, a.nx, a.ny, a.nz);
-        f[i] = Pop<T>::ld(a.fin, (size_t)i * a.np + src, R(0));
-    }
+    for (int i = 0; i < L::Q; ++i, p += a.np) f[i] = Pop<T>::ld(p, nbr_offset<L>(o, i, -1), R(0));
     const int fl = a.flags[c.n];
     const int type = fl & 7;
     if (type == WALL)
@@ -414,12 +429,24 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
             a0 = u0; a1 = u1; a2 = u2; amp = g;
         }
         const R uu = a0 * a0 + a1 * a1 + a2 * a2;
-        const R om = a.omega;
+        const R om = a.omega, om1 = R(1) - om;
+        // h_eq,i = w_i (drho + k (3 e_i.a + 4.5 (e_i.a)^2 - 1.5 a.a)), k = rho0 amp.
+        // A direction and its opposite share the even part and negate the odd
+        // one, so each pair is evaluated once; 1/tau is folded into w_i.
+        const R k = a.rho0 * amp;
+        const R ev = drho - R(1.5) * k * uu;
+        const R k45 = R(4.5) * k, k3 = R(3) * k;
+        f[0] = om1 * f[0] + (om * R(L::w(0))) * ev;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
+        for (int i = 1; i < L::Q; ++i) {
+            if (L::opp(i) < i) continue;
+            const int j = L::opp(i);
+            const R omw = om * R(L::w(i));
             const R eu = R(L::cx(i)) * a0 + R(L::cy(i)) * a1 + R(L::cz(i)) * a2;
-            const R heq = R(L::w(i)) * (drho + a.rho0 * amp * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
-            f[i] += om * (heq - f[i]);
+            const R even = omw * (ev + k45 * eu * eu);
+            const R odd = (omw * k3) * eu;
+            f[i] = om1 * f[i] + (even + odd);
+            f[j] = om1 * f[j] + (even - odd);
         }
     }
 #pragma unroll
@@ -464,30 +491,35 @@ __global__ void k_flow_init(FlowArgs<T, TA, R> a, int which) {
 template <class L, typename R>
 struct AdjMoments {
     R A, M0, M1, M2, Q00, Q11, Q22, Q01, Q02, Q12;
+    // a direction and its opposite enter A and Q through their sum and M
+    // through their difference (e_opp = -e), so each pair is read once
     __device__ __forceinline__ void compute(const R (&s)[L::Q]) {
-        A = M0 = M1 = M2 = Q00 = Q11 = Q22 = Q01 = Q02 = Q12 = R(0);
+        M0 = M1 = M2 = Q00 = Q11 = Q22 = Q01 = Q02 = Q12 = R(0);
+        A = R(L::w(0)) * s[0];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const R ws = R(L::w(i)) * s[i];
+        for (int i = 1; i < L::Q; ++i) {
+            if (L::opp(i) < i) continue;
+            const int j = L::opp(i);
+            const R wp = R(L::w(i)) * (s[i] + s[j]);
+            const R wd = R(L::w(i)) * (s[i] - s[j]);
             const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-            A += ws;
-            if (x) { M0 += R(x) * ws; Q00 += ws; }
-            if (y) { M1 += R(y) * ws; Q11 += ws; }
-            if (z) { M2 += R(z) * ws; Q22 += ws; }
-            if (x * y) Q01 += R(x * y) * ws;
-            if (x * z) Q02 += R(x * z) * ws;
-            if (y * z) Q12 += R(y * z) * ws;
+            A += wp;
+            if (x) { M0 += R(x) * wd; Q00 += wp; }
+            if (y) { M1 += R(y) * wd; Q11 += wp; }
+            if (z) { M2 += R(z) * wd; Q22 += wp; }
+            if (x * y) Q01 += R(x * y) * wp;
+            if (x * z) Q02 += R(x * z) * wp;
+            if (y * z) Q12 += R(y * z) * wp;
         }
     }
 };
 
 template <class L, typename T, typename TA, typename R>
 __device__ __forceinline__ void pull_adjoint(const FlowArgs<T, TA, R>& a, const Cell& c, R (&s)[L::Q]) {
+    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+    const TA* __restrict__ p = a.ain + c.n;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const long long src = shifted<L>(c, i, +1, a.nx, a.ny, a.nz);
-        s[i] = Pop<TA>::ld(a.ain, (size_t)i * a.np + src, R(0)) * a.ascale;
-    }
+    for (int i = 0; i < L::Q; ++i, p += a.np) s[i] = Pop<TA>::ld(p, nbr_offset<L>(o, i, +1), R(0)) * a.ascale;
 }
 
 // resident 256-thread blocks per SM requested from the compiler: the plain
@@ -536,9 +568,16 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
         w0 = om * w0 + v0;
         w1 = om * w1 + v1;
         w2 = om * w2 + v2;
+        const R om1 = R(1) - om;
+        s[0] = om1 * s[0] + base;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i)
-            s[i] = (R(1) - om) * s[i] + base + R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
+        for (int i = 1; i < L::Q; ++i) {
+            if (L::opp(i) < i) continue;
+            const int j = L::opp(i);
+            const R ew = R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
+            s[i] = om1 * s[i] + (base + ew);
+            s[j] = om1 * s[j] + (base - ew);
+        }
         if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
     }
     const R inv = R(1) / a.ascale;
@@ -647,11 +686,11 @@ __device__ __forceinline__ void thermal_bc(R (&g)[7], int fl, const R* __restric
 template <typename T, typename TA, typename R>
 __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const Cell& c, R (&g)[7],
                                             R& gam, R& u0, R& u1, R& u2) {
+    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+    const T* __restrict__ p = a.gin + c.n;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const long long src = shifted<D3Q7>(c, k, -1, a.nx, a.ny, a.nz);
-        g[k] = Pop<T>::ld(a.gin, (size_t)k * a.np + src, R(D3Q7::w(k)) * a.T0);
-    }
+    for (int k = 0; k < 7; ++k, p += a.np)
+        g[k] = Pop<T>::ld(p, nbr_offset<D3Q7>(o, k, -1), R(D3Q7::w(k)) * a.T0);
     const int fl = a.flags[c.n];
     gam = a.gamma[c.n];
     u0 = a.u[c.n];
@@ -733,11 +772,10 @@ __device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, 
 
 template <typename T, typename TA, typename R>
 __device__ __forceinline__ void thermal_pull_adjoint(const ThermArgs<T, TA, R>& a, const Cell& c, R (&s)[7]) {
+    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+    const TA* __restrict__ p = a.ain + c.n;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const long long src = shifted<D3Q7>(c, k, +1, a.nx, a.ny, a.nz);
-        s[k] = Pop<TA>::ld(a.ain, (size_t)k * a.np + src, R(0)) * a.ascale;
-    }
+    for (int k = 0; k < 7; ++k, p += a.np) s[k] = Pop<TA>::ld(p, nbr_offset<D3Q7>(o, k, +1), R(0)) * a.ascale;
 }
 
 template <typename T, typename TA, typename R, bool REDUCE>
@@ -848,11 +886,12 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
                 if (k == kn) en = ecomp<R>(k, u0, u1, u2);
             const R wa = R(0.125) * (R(1) + R(4) * gam * en);
             R K = 0;
+            const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
                 if (k == kn) continue;
-                const long long src = shifted<D3Q7>(c, k, -1, a.nx, a.ny, a.nz);
-                K += Pop<T>::ld(a.gin, (size_t)k * a.np + src, R(D3Q7::w(k)) * a.T0);
+                K += Pop<T>::ld(a.gin + (long long)k * a.np + c.n, nbr_offset<D3Q7>(o, k, -1),
+                                R(D3Q7::w(k)) * a.T0);
             }
             const R dgda = R(0.125) * K / ((R(1) - wa) * (R(1) - wa));
             const R ckn = a.gcn[c.n];
