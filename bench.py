@@ -240,8 +240,8 @@ def run_batchcmp(args):
             s.close()
         return dt
 
-    def batched(lats, steps):
-        b = Batch("fp32", 500, 32)
+    def batched(lats, steps, solo_tiles=None):
+        b = Batch("fp32", 500, 32, solo_tiles)
         ss = [Solver.from_lattice(l, device="cuda:0") for l in lats]
         for s in ss:
             b.admit(s, 0.0, 1000, True)
@@ -264,13 +264,19 @@ def run_batchcmp(args):
     cases = [("1 x 192x96x48", [I.pipe_bend_3d(n=192, ny=96, nz=48, width=12, re=20.0)], 4000),
              ("1 x 64^3", [I.pipe_bend_3d(n=64, re=20.0)], 10000),
              ("4 x 64^3", [I.pipe_bend_3d(n=64, re=20.0, seed=k) for k in range(4)], 4000),
-             ("16 x 32^3", [I.pipe_bend_3d(n=32, re=20.0, seed=k) for k in range(16)], 4000)]
+             ("16 x 32^3", [I.pipe_bend_3d(n=32, re=20.0, seed=k) for k in range(16)], 4000),
+             ("mix 32^3+64^3+96x48x24+128x64x32+192x96x48",
+              [I.pipe_bend_3d(n=32, re=20.0), I.pipe_bend_3d(n=64, re=20.0),
+               I.pipe_bend_3d(n=96, ny=48, nz=24, width=12, re=20.0),
+               I.pipe_bend_3d(n=128, ny=64, nz=32, width=16, re=20.0),
+               I.pipe_bend_3d(n=192, ny=96, nz=48, width=12, re=20.0)], 4000)]
     out = {"mode": "batchcmp", "storage": "fp32", "steps": "forward N + adjoint N per lattice"}
     for name, lats, steps in cases:
         nodes = sum(l.n for l in lats)
-        ts, tb = single(lats, steps), batched(lats, steps)
+        ts, tb, tp = single(lats, steps), batched(lats, steps), batched(lats, steps, 0)
         out[name] = {"single_MLUPS": round(2 * nodes * steps / ts / 1e6, 1),
-                     "batched_MLUPS": round(2 * nodes * steps / tb / 1e6, 1)}
+                     "batched_MLUPS": round(2 * nodes * steps / tb / 1e6, 1),
+                     "packed_only_MLUPS": round(2 * nodes * steps / tp / 1e6, 1)}
     print(json.dumps(out))
 
 

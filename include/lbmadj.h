@@ -203,8 +203,12 @@ lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
  * lbm_adjoint do (same step counts, same FP64 sums), so a context's results
  * are bit-identical alone, in any mix, and through the single-context calls.
  * Contexts may be admitted and retired between steps (continuous batching);
- * admission never re-captures the graph.  Built for D3Q19 with FP32, FP16_OFS
- * or BF16_OFS storage.
+ * admission never re-captures the graph.  A lattice large enough to fill the
+ * GPU on its own (by default: at least one wave of the persistent launch,
+ * see lbm_batch_set_solo_tiles) runs its K steps as its own single-lattice
+ * graph on its context's stream, concurrently with the packed launch; its
+ * results are those of the single-context calls by construction.  Built for
+ * D3Q19 with FP32, FP16_OFS or BF16_OFS storage.
  * --------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
@@ -231,6 +235,12 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* ctx, const lbm_solve_opts* opt
  * contexts whose phase converged (or hit its cap, or diverged) on; *n_active
  * receives the contexts still running.  Synchronises. */
 lbm_status lbm_batch_step(lbm_batch* b, int* n_active);
+
+/* Contexts admitted from now on whose lattice has at least min_tiles tiles
+ * (256-node blocks of its single-lattice launch) run solo; 0 packs every
+ * lattice into the persistent launch.  The default is the persistent launch's
+ * resident block count (SMs x blocks per SM).  Errors: LBM_ERR_ARG. */
+lbm_status lbm_batch_set_solo_tiles(lbm_batch* b, long long min_tiles);
 
 /* Contexts that finished since the last poll: up to max (slot, context,
  * report) triples; *n receives the count.  A finished context is released

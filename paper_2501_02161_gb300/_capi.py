@@ -80,6 +80,7 @@ SIGNATURES = {
     "lbm_batch_destroy": (None, [_VP]),
     "lbm_batch_admit": (_I, [_VP, _VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(_I)]),
     "lbm_batch_step": (_I, [_VP, ctypes.POINTER(_I)]),
+    "lbm_batch_set_solo_tiles": (_I, [_VP, ctypes.c_longlong]),
     "lbm_batch_poll": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(lbm_report),
                             _I, ctypes.POINTER(_I)]),
     "lbm_last_error": (ctypes.c_char_p, []),

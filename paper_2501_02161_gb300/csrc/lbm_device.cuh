@@ -933,16 +933,22 @@ struct BatchConst {
 // one persistent launch per step covers the tiles of every resident lattice,
 // each tile dispatching on its lattice's phase (uniform within a block):
 // 0 flow, 1 temperature, 2 flow adjoint, 3 temperature adjoint.  A tile entry
-// is (slot | z << 8, x0, y0, block id), so no division is needed.
+// is (slot | z << 8, x0, y0, block id), so no division is needed.  The next
+// tile's entry is loaded before the current tile is computed, so a block never
+// waits on the tile table between tiles.  Four 256-thread blocks per SM leave
+// 64 registers a thread: the union of the four node functions and the tile
+// loop does not fit the single kernels' 40-48 without spilling.
 template <class L, typename T, typename TG, typename TA, typename R, bool REDUCE, class Bank>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 4)
     k_batch(const int4* __restrict__ tiles, const int* __restrict__ ntiles, int step) {
     const BatchConst<T, TG, TA, R>& C = Bank::get();
     pdl_launch_dependents();
     pdl_wait();
     const int nt = *ntiles;
+    int4 next = blockIdx.x < nt ? tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int4 tl = tiles[t];
+        const int4 tl = next;
+        if (t + (int)gridDim.x < nt) next = tiles[t + gridDim.x];
         const int sl = tl.x & 0xff;
         const int par = (C.cur[sl] + step) & 1;
         const int4 g = C.geom[sl];

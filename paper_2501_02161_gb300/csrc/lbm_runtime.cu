@@ -800,6 +800,7 @@ struct BatchEntry {
     int status = LBM_OK;     // worst warning / first error
     double t0 = 0;
     bool used = false;
+    bool solo = false;       // runs its own single-lattice graph (large lattice)
 };
 
 }  // namespace
@@ -810,6 +811,7 @@ struct lbm_batch {
     int K = 1000;
     int max_slots = 0;
     int grid = 0;
+    long long solo_tiles = 0; // lattices with at least this many tiles run solo (0: never)
     cudaStream_t stream = nullptr;
     std::vector<char> h_bank;   // host image of the __constant__ argument bank
     int4* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -852,7 +854,7 @@ lbm_status batch_upload(lbm_batch* b) {
     std::vector<int> list;
     for (int i = 0; i < b->max_slots; ++i) {
         BatchEntry& en = b->e[i];
-        if (!en.used || en.phase == SP_DONE) continue;
+        if (!en.used || en.phase == SP_DONE || en.solo) continue;
         batch_slot_refresh(b, i);
         const Geom& g = en.ctx->geom;
         // the single-lattice launch's blocks, in its block-id order
@@ -888,11 +890,16 @@ lbm_status batch_upload(lbm_batch* b) {
     return LBM_OK;
 }
 
+// phases present among the packed (not solo) running entries
 int batch_mask(lbm_batch* b) {
     int m = 0;
     for (int i = 0; i < b->max_slots; ++i)
-        if (b->e[i].used && b->e[i].phase != SP_DONE) m |= 1 << b->e[i].phase;
+        if (b->e[i].used && !b->e[i].solo && b->e[i].phase != SP_DONE) m |= 1 << b->e[i].phase;
     return m;
+}
+
+int slot_to_ctx_phase(int ph) {
+    return ph == SP_FLOW ? PH_FLOW : (ph == SP_THERM ? PH_THERM : (ph == SP_ADJ ? PH_ADJ : PH_TADJ));
 }
 
 cudaError_t batch_enqueue(lbm_batch* b) {
@@ -1007,6 +1014,7 @@ lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int m
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     b->grid = std::max(1, sms) * batch_blocks_per_sm(storage);
+    b->solo_tiles = b->grid;
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_lists, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 8);
@@ -1067,6 +1075,7 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* c, const lbm_solve_opts* o, in
     en.tol = o->tol;
     en.max_steps = o->max_steps;
     en.t0 = now_ms();
+    en.solo = b->solo_tiles > 0 && c->geom.nblocks >= b->solo_tiles;
     b->dirty = true;
     if (slot) *slot = i;
     return LBM_OK;
@@ -1087,11 +1096,21 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
         lbm_status st = batch_upload(b);
         if (st != LBM_OK) return st;
     }
+    // solo entries: K steps of the context's own single-lattice graph on its
+    // stream, running concurrently with the packed launch below
+    bool any_solo = false;
+    for (int i = 0; i < b->max_slots; ++i) {
+        BatchEntry& en = b->e[i];
+        if (!en.used || en.phase == SP_DONE || !en.solo) continue;
+        lbm_status st = run_block(en.ctx, slot_to_ctx_phase(en.phase), b->K);
+        if (st != LBM_OK) return st;
+        any_solo = true;
+    }
     const int mask = batch_mask(b);
-    if (mask) {
+    if (mask || any_solo) {
         const int key = 0;  // one graph: the tables it reads live in device memory
         auto it = b->graphs.find(key);
-        if (it == b->graphs.end()) {
+        if (mask && it == b->graphs.end()) {
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = batch_enqueue(b);
@@ -1107,16 +1126,20 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
             if (e3 != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e3));
             it = b->graphs.emplace(key, x).first;
         }
-        CUDA_TRY(cudaGraphLaunch(it->second, b->stream));
+        if (mask) CUDA_TRY(cudaGraphLaunch(it->second, b->stream));
         CUDA_TRY(cudaStreamSynchronize(b->stream));
+        for (int i = 0; i < b->max_slots; ++i) {
+            BatchEntry& en = b->e[i];
+            if (en.used && en.phase != SP_DONE && en.solo) CUDA_TRY(cudaStreamSynchronize(en.ctx->stream));
+        }
         for (int i = 0; i < b->max_slots; ++i) {
             BatchEntry& en = b->e[i];
             if (!en.used || en.phase == SP_DONE) continue;
             lbm_ctx* c = en.ctx;
             const int ph = en.phase;
             // map the slot phase to the context's residual bookkeeping
-            const int cph = ph == SP_FLOW ? PH_FLOW : (ph == SP_THERM ? PH_THERM : (ph == SP_ADJ ? PH_ADJ : PH_TADJ));
-            const double* r = b->h_results + 2 * i;
+            const int cph = slot_to_ctx_phase(ph);
+            const double* r = en.solo ? c->hres : b->h_results + 2 * i;
             const double denom = (double)(c->n_nw > 0 ? c->n_nw : 1);
             const double cur = r[0] / denom;
             if (ph == SP_FLOW) c->J_p = c->n_in > 0 ? c->obj.w_pin * r[1] / (3.0 * (double)c->n_in) : 0.0;
@@ -1145,6 +1168,13 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
         for (int i = 0; i < b->max_slots; ++i) n += b->e[i].used && b->e[i].phase != SP_DONE;
         *n_active = n;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_solo_tiles(lbm_batch* b, long long min_tiles) {
+    if (!b) return fail(LBM_ERR_ARG, "batch is null");
+    if (min_tiles < 0) return fail(LBM_ERR_ARG, "min_tiles < 0");
+    b->solo_tiles = min_tiles;
     return LBM_OK;
 }
 

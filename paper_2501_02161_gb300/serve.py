@@ -14,8 +14,10 @@ this module only schedules.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import time
 from collections import OrderedDict, deque
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -92,6 +94,36 @@ def lattice_for(req: Request):
                           seed=req.seed % 100000)
 
 
+class LatticePrep:
+    """Builds the lattices of the next few requests on worker threads while the
+    GPU works (host numpy only; a lattice is a pure function of its request, so
+    results do not change).  Both the server and the sequential baseline use it."""
+
+    def __init__(self, workers: int = 2, ahead: int = 8):
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self.futs = {}
+        self.ahead = ahead
+
+    def want(self, reqs, skip=lambda r: False):
+        """Start building the first `ahead` requests of `reqs` (in order)."""
+        for r in itertools.islice((r for r in reqs if not skip(r)), self.ahead):
+            if r.rid not in self.futs:
+                self.futs[r.rid] = self.pool.submit(lattice_for, r)
+
+    def get(self, req):
+        f = self.futs.pop(req.rid, None)
+        return f.result() if f is not None else lattice_for(req)
+
+    def drop(self, req):
+        f = self.futs.pop(req.rid, None)
+        if f is not None:
+            f.cancel()
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+        self.futs.clear()
+
+
 def footprint(lat, storage: str) -> int:
     return int(C.lib().lbm_footprint_bytes(lat.stencil, lat.nx, lat.ny, lat.nz,
                                            STORAGES[storage], int(lat.thermal)))
@@ -108,11 +140,18 @@ def opt_step_gamma(lat, gamma: torch.Tensor, sens: torch.Tensor, step: float = 0
 class Batch:
     """Thin owner of an lbm_batch (same names as the C-ABI)."""
 
-    def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 32):
+    def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 32,
+                 solo_tiles: int | None = None):
+        """solo_tiles: lattices with at least this many 256-node tiles run their
+        own single-lattice graph beside the packed launch (0: pack every
+        lattice; None: the library's default, one wave of the packed launch)."""
         self.lib = C.lib()
         self._b = ctypes.c_void_p()
         C.check(self.lib.lbm_batch_create(ctypes.byref(self._b), STORAGES[storage],
                                           int(check_every), int(max_slots)), "lbm_batch_create")
+        if solo_tiles is not None:
+            C.check(self.lib.lbm_batch_set_solo_tiles(self._b, int(solo_tiles)),
+                    "lbm_batch_set_solo_tiles")
         self.max_slots = max_slots
         self._slots = (ctypes.c_int * max_slots)()
         self._ctxs = (ctypes.c_void_p * max_slots)()
@@ -159,7 +198,7 @@ class Server:
     def __init__(self, storage: str = "fp32", budget_bytes: int | None = None,
                  check_every: int = 500, max_slots: int = 32, tol: float = 1e-4,
                  max_steps: int = 20000, keep_designs: bool = True, device=None,
-                 max_active_nodes: int = 6_000_000):
+                 max_active_nodes: int = 1_000_000, solo_tiles: int | None = None):
         self.device = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
         self.storage = storage
         if budget_bytes is None:
@@ -169,13 +208,15 @@ class Server:
         self.used = 0
         self.tol, self.max_steps = tol, max_steps
         self.keep = keep_designs
-        # beyond a few million resident nodes one graph replay already keeps
-        # every SM busy; admitting more only lengthens everyone's latency
+        # about a million in-flight nodes (one 192x96x48 lattice plus small
+        # ones) already keep every SM busy; admitting more only shares the GPU
+        # among more requests and lengthens everyone's latency
         self.max_active_nodes = max_active_nodes
-        self.batch = Batch(storage, check_every, max_slots)
+        self.batch = Batch(storage, check_every, max_slots, solo_tiles)
         self.max_slots = max_slots
         self.resident = OrderedDict()   # design id -> (solver, lattice, gamma, last sens, bytes)
         self.active = {}                # ctx pointer value -> (request, result, design id)
+        self.prep = LatticePrep()
 
     def _evict_one(self) -> bool:
         busy = {d for (_, _, d) in self.active.values()}
@@ -186,6 +227,10 @@ class Server:
                 self.used -= nb
                 return True
         return False
+
+    def _warm_ready(self, req) -> bool:
+        ent = self.resident.get(req.design)
+        return req.kind == "opt" and ent is not None and ent[3] is not None
 
     def _active_nodes(self) -> int:
         return sum(int(np.prod(r.shape)) for (r, _, _) in self.active.values())
@@ -206,8 +251,9 @@ class Server:
             s.set_gamma(gamma)
             self.resident[d] = (s, lat, gamma, sens, nb)
             warm = True
+            self.prep.drop(req)
         else:
-            lat = lattice_for(req)
+            lat = self.prep.get(req)
             nb = footprint(lat, self.storage)
             while self.used + nb > self.budget:
                 if not self._evict_one():
@@ -240,6 +286,7 @@ class Server:
             now = time.perf_counter() - t0 if realtime else float("inf")
             while order and order[0].arrival <= now:
                 waiting.append(order.popleft())
+            self.prep.want(waiting, skip=self._warm_ready)
             # admission: arrival order, except that a request whose design is
             # still being solved lets later requests for other designs pass;
             # the first request that does not fit in memory stops admission
@@ -287,6 +334,7 @@ class Server:
         return [results[r.rid] for r in requests]
 
     def close(self):
+        self.prep.close()
         for d in list(self.resident):
             self.resident.pop(d)[0].close()
         self.batch.close()
@@ -302,21 +350,27 @@ def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_ste
     dev = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
     designs = OrderedDict()
     results = []
+    prep = LatticePrep()
+    ordered = sorted(requests, key=lambda r: r.arrival)
+    warm_ready = lambda r: r.kind == "opt" and r.design in designs and designs[r.design][3] is not None
     t0 = time.perf_counter()
-    for req in sorted(requests, key=lambda r: r.arrival):
+    for k, req in enumerate(ordered):
         if realtime:
             wait = req.arrival - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
+        now = time.perf_counter() - t0 if realtime else float("inf")
+        prep.want(itertools.takewhile(lambda r: r.arrival <= now, ordered[k:]), skip=warm_ready)
         res = Result(req.rid, req.kind, req.arrival, admitted=time.perf_counter() - t0)
         warm = False
-        if req.kind == "opt" and req.design in designs and designs[req.design][3] is not None:
+        if warm_ready(req):
             s, lat, gamma, sens = designs[req.design]
             gamma = opt_step_gamma(lat, gamma, sens)
             s.set_gamma(gamma)
             warm = True
+            prep.drop(req)
         else:
-            lat = lattice_for(req)
+            lat = prep.get(req)
             if req.design in designs:
                 designs.pop(req.design)[0].close()
             s = Solver.from_lattice(lat, storage=storage, device=dev)
@@ -346,6 +400,7 @@ def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_ste
         else:
             designs.pop(req.design, None)  # the design's state is no longer usable
             s.close()
+    prep.close()
     for v in designs.values():
         v[0].close()
     return sorted(results, key=lambda r: r.rid)

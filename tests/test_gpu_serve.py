@@ -33,10 +33,10 @@ def mix():
             I.heat_sink(nx=40, ny=20, nz=12, re=15.0, q_flux=2e-3, seed=6)]
 
 
-def solve_batched(lats, storage="fp32", tol=1e-5, max_steps=20000, order=None):
+def solve_batched(lats, storage="fp32", tol=1e-5, max_steps=20000, order=None, solo_tiles=None):
     from paper_2501_02161_gb300.serve import Batch
     from paper_2501_02161_gb300.solver import Solver
-    b = Batch(storage, K, 8)
+    b = Batch(storage, K, 8, solo_tiles)
     solvers = [Solver.from_lattice(l, storage=storage) for l in lats]
     for k in (order or range(len(lats))):
         b.admit(solvers[k], tol, max_steps, reset=True)
@@ -54,10 +54,13 @@ def solve_batched(lats, storage="fp32", tol=1e-5, max_steps=20000, order=None):
     return out
 
 
-def test_batched_equals_single_context_bitwise():
+# solo_tiles: None = library default (these lattices are all packed), 0 = all
+# packed, 1 = every lattice on its own graph, 40 = some of each
+@pytest.mark.parametrize("solo_tiles", [None, 1, 40])
+def test_batched_equals_single_context_bitwise(solo_tiles):
     from paper_2501_02161_gb300.solver import Solver
     lats = mix()
-    got = solve_batched(lats)
+    got = solve_batched(lats, solo_tiles=solo_tiles)
     for lat, (rep, sens, u) in zip(lats, got):
         s = Solver.from_lattice(lat, storage="fp32")
         rf = s.forward(tol=1e-5, max_steps=20000, check_every=K)
