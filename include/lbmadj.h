@@ -193,6 +193,36 @@ lbm_status lbm_get_adjoint(lbm_ctx* ctx, void* fstar, void* gstar, int dtype, in
 lbm_status lbm_time_steps(lbm_ctx* ctx, int phase, int n, double* ms_per_step);
 
 /* ---------------------------------------------------------------------------
+ * Checkpoint / resume of a context's solver state (no counterpart in the
+ * paper).  The state is the current forward and adjoint populations (and the
+ * temperature ones), the frozen fields the adjoint reads, and the solve
+ * bookkeeping (which phases completed, the last residual quantities, J); the
+ * inputs (flags, gamma, BC values, parameters) are not part of it.  A state
+ * imported into a context of the same shape, stencil, storage and thermal
+ * setting, whose flags and parameters were set to the same values, continues
+ * exactly as the exporting context would: a warm-started lbm_forward /
+ * lbm_adjoint, lbm_sensitivity and lbm_get_fields give bit-identical results.
+ * Use it to move a design's state off the device and back, or to checkpoint
+ * a long solve.
+ * --------------------------------------------------------------------------- */
+
+/* Bytes lbm_export_state writes for this context (0 for a null context). */
+size_t lbm_state_bytes(lbm_ctx* ctx);
+
+/* Copy the state to dst (host memory, pinned or pageable, or device memory;
+ * at least lbm_state_bytes(ctx) bytes, owned by the caller).  Synchronises.
+ * Errors: LBM_ERR_ARG (null pointer, buffer too small), LBM_ERR_CUDA. */
+lbm_status lbm_export_state(lbm_ctx* ctx, void* dst, size_t bytes);
+
+/* Replace the context's state with one written by lbm_export_state.  The
+ * flags and parameters must already be set to the values the state was
+ * computed with (LBM_ERR_ARG otherwise, or when the shape, stencil, storage
+ * or thermal setting differ, or the buffer is short); gamma may differ (a
+ * warm start after a design update).  Synchronises.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_CUDA. */
+lbm_status lbm_import_state(lbm_ctx* ctx, const void* src, size_t bytes);
+
+/* ---------------------------------------------------------------------------
  * Batched solves (serving)
  *
  * A batch advances many resident contexts together: every call of

@@ -79,6 +79,9 @@ SIGNATURES = {
     "lbm_batch_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I]),
     "lbm_batch_destroy": (None, [_VP]),
     "lbm_batch_admit": (_I, [_VP, _VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(_I)]),
+    "lbm_state_bytes": (ctypes.c_size_t, [_VP]),
+    "lbm_export_state": (_I, [_VP, _VP, ctypes.c_size_t]),
+    "lbm_import_state": (_I, [_VP, _VP, ctypes.c_size_t]),
     "lbm_batch_step": (_I, [_VP, ctypes.POINTER(_I)]),
     "lbm_batch_set_solo_tiles": (_I, [_VP, ctypes.c_longlong]),
     "lbm_batch_poll": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(lbm_report),

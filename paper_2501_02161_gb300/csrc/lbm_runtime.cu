@@ -738,6 +738,137 @@ lbm_status lbm_get_adjoint(lbm_ctx* c, void* fstar, void* gstar, int dtype, int 
     return leave(c);
 }
 
+// ---------------------------------------------------------------------------
+// state checkpoint: a header, then the current buffer of every population set
+// and the fields a resumed solve reads (plain copies, any memory kind)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct StateHeader {
+    char magic[8];  // "LBMSTATE"
+    int version;
+    int stencil, storage, thermal;
+    int nx, ny, nz;
+    long long np, n_in, n_nw;
+    int fstate, astate, fwd_done, adj_done;
+    double J_p, J_T;
+    double last_I[4];
+    double tau, rho0;
+};
+
+struct StatePart {
+    void* buf;
+    size_t bytes;
+};
+
+std::vector<StatePart> state_parts(lbm_ctx* c) {
+    const size_t np = (size_t)c->np;
+    std::vector<StatePart> v;
+    v.push_back({c->f[c->fcur], np * c->Q * c->pb});
+    v.push_back({c->fa[c->facur], np * c->Q * c->ab});
+    v.push_back({c->rho, np * c->rb});
+    v.push_back({c->u, np * 3 * c->rb});
+    if (c->thermal) {
+        v.push_back({c->g[c->gcur], np * 7 * heat_bytes(c->storage)});
+        v.push_back({c->ga[c->gacur], np * 7 * c->ab});
+        v.push_back({c->T, np * c->rb});
+        v.push_back({c->gpost, np * 7 * c->rb});
+        v.push_back({c->gcn, np * c->rb});
+        v.push_back({c->cpl, np * 3 * c->rb});
+        v.push_back({c->sT, np * c->rb});
+    }
+    return v;
+}
+
+constexpr size_t kStateAlign = 256;
+
+size_t state_size(lbm_ctx* c) {
+    size_t b = (sizeof(StateHeader) + kStateAlign - 1) / kStateAlign * kStateAlign;
+    for (const StatePart& p : state_parts(c)) b += (p.bytes + kStateAlign - 1) / kStateAlign * kStateAlign;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_state_bytes(lbm_ctx* c) { return c ? state_size(c) : 0; }
+
+lbm_status lbm_export_state(lbm_ctx* c, void* dst, size_t bytes) {
+    if (!c || !dst) return fail(LBM_ERR_ARG, "null argument");
+    if (bytes < state_size(c)) return fail(LBM_ERR_ARG, "state buffer smaller than lbm_state_bytes");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LBMSTATE", 8);
+    h.version = 1;
+    h.stencil = c->stencil;
+    h.storage = c->storage;
+    h.thermal = c->thermal;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.np = c->np;
+    h.n_in = c->n_in;
+    h.n_nw = c->n_nw;
+    h.fstate = c->fstate;
+    h.astate = c->astate;
+    h.fwd_done = c->fwd_done;
+    h.adj_done = c->adj_done;
+    h.J_p = c->J_p;
+    h.J_T = c->J_T;
+    for (int k = 0; k < 4; ++k) h.last_I[k] = c->last_I[k];
+    h.tau = c->prm.tau;
+    h.rho0 = c->prm.rho0;
+    char* d = (char*)dst;
+    size_t off = (sizeof(StateHeader) + kStateAlign - 1) / kStateAlign * kStateAlign;
+    for (const StatePart& p : state_parts(c)) {
+        CUDA_TRY(cudaMemcpyAsync(d + off, p.buf, p.bytes, cudaMemcpyDefault, c->stream));
+        off += (p.bytes + kStateAlign - 1) / kStateAlign * kStateAlign;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyDefault, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return leave(c);
+}
+
+lbm_status lbm_import_state(lbm_ctx* c, const void* src, size_t bytes) {
+    if (!c || !src) return fail(LBM_ERR_ARG, "null argument");
+    if (bytes < sizeof(StateHeader)) return fail(LBM_ERR_ARG, "state buffer smaller than its header");
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    StateHeader h;
+    CUDA_TRY(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 1)
+        return fail(LBM_ERR_ARG, "not a state written by lbm_export_state");
+    if (h.stencil != c->stencil || h.storage != c->storage || h.thermal != (int)c->thermal ||
+        h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.np != c->np)
+        return fail(LBM_ERR_ARG, "state is for another lattice shape, stencil, storage or thermal setting");
+    if (!c->have_flags || !c->have_params || h.n_in != c->n_in || h.n_nw != c->n_nw ||
+        h.tau != c->prm.tau || h.rho0 != c->prm.rho0)
+        return fail(LBM_ERR_ARG, "set the same flags and parameters before importing a state");
+    if (bytes < state_size(c)) return fail(LBM_ERR_ARG, "state buffer smaller than lbm_state_bytes");
+    c->fcur = c->facur = c->gcur = c->gacur = 0;
+    const char* s = (const char*)src;
+    size_t off = (sizeof(StateHeader) + kStateAlign - 1) / kStateAlign * kStateAlign;
+    for (const StatePart& p : state_parts(c)) {
+        CUDA_TRY(cudaMemcpyAsync(p.buf, s + off, p.bytes, cudaMemcpyDefault, c->stream));
+        off += (p.bytes + kStateAlign - 1) / kStateAlign * kStateAlign;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->fstate = h.fstate;
+    c->astate = h.astate;
+    c->fwd_done = h.fwd_done;
+    c->adj_done = h.adj_done;
+    c->J_p = h.J_p;
+    c->J_T = h.J_T;
+    for (int k = 0; k < 4; ++k) c->last_I[k] = h.last_I[k];
+    return leave(c);
+}
+
 lbm_status lbm_time_steps(lbm_ctx* c, int phase, int n, double* ms_per_step) {
     lbm_status st = ready(c);
     if (st != LBM_OK) return st;

@@ -129,6 +129,13 @@ def footprint(lat, storage: str) -> int:
                                            STORAGES[storage], int(lat.thermal)))
 
 
+def footprint_of(req: Request, storage: str) -> int:
+    """Device bytes of the context a request needs (without building its lattice)."""
+    nx, ny, nz = req.shape
+    return int(C.lib().lbm_footprint_bytes(C.LBM_D3Q19, nx, ny, nz, STORAGES[storage],
+                                           int(req.thermal)))
+
+
 def opt_step_gamma(lat, gamma: torch.Tensor, sens: torch.Tensor, step: float = 0.05) -> torch.Tensor:
     """One projected-gradient update of the design nodes (fluid nodes)."""
     design = torch.as_tensor((lat.flags & 7) == I.FLUID, device=gamma.device)
@@ -198,7 +205,8 @@ class Server:
     def __init__(self, storage: str = "fp32", budget_bytes: int | None = None,
                  check_every: int = 500, max_slots: int = 32, tol: float = 1e-4,
                  max_steps: int = 20000, keep_designs: bool = True, device=None,
-                 max_active_nodes: int = 1_000_000, solo_tiles: int | None = None):
+                 max_active_nodes: int = 1_000_000, solo_tiles: int | None = None,
+                 host_budget_bytes: int = 32 << 30):
         self.device = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
         self.storage = storage
         if budget_bytes is None:
@@ -215,14 +223,28 @@ class Server:
         self.batch = Batch(storage, check_every, max_slots, solo_tiles)
         self.max_slots = max_slots
         self.resident = OrderedDict()   # design id -> (solver, lattice, gamma, last sens, bytes)
+        self.offloaded = OrderedDict()  # design id -> (lattice, gamma, last sens, host state)
+        self.host_used = 0
+        self.host_budget = host_budget_bytes
+        self.n_restored = 0             # designs brought back from host memory
         self.active = {}                # ctx pointer value -> (request, result, design id)
         self.prep = LatticePrep()
 
     def _evict_one(self) -> bool:
+        """Free the least recently used idle design's device memory; a design
+        with a finished solve keeps its state in host memory (export_state) so
+        a later optimisation step still warm-starts."""
         busy = {d for (_, _, d) in self.active.values()}
         for d in list(self.resident):
             if d not in busy:
-                s, _, _, _, nb = self.resident.pop(d)
+                s, lat, gamma, sens, nb = self.resident.pop(d)
+                if self.keep and sens is not None:
+                    state = s.export_state()
+                    self.offloaded[d] = (lat, gamma.cpu(), sens, state)
+                    self.offloaded.move_to_end(d)
+                    self.host_used += state.numel()
+                    while self.host_used > self.host_budget and self.offloaded:
+                        self.host_used -= self.offloaded.popitem(last=False)[1][3].numel()
                 s.close()
                 self.used -= nb
                 return True
@@ -230,10 +252,17 @@ class Server:
 
     def _warm_ready(self, req) -> bool:
         ent = self.resident.get(req.design)
-        return req.kind == "opt" and ent is not None and ent[3] is not None
+        return req.kind == "opt" and ((ent is not None and ent[3] is not None)
+                                      or req.design in self.offloaded)
 
     def _active_nodes(self) -> int:
         return sum(int(np.prod(r.shape)) for (r, _, _) in self.active.values())
+
+    def _make_room(self, nb: int) -> bool:
+        while self.used + nb > self.budget:
+            if not self._evict_one():
+                return False
+        return True
 
     def _admit(self, req: Request, res: Result, now: float) -> bool:
         if len(self.active) >= self.max_slots:
@@ -252,21 +281,39 @@ class Server:
             self.resident[d] = (s, lat, gamma, sens, nb)
             warm = True
             self.prep.drop(req)
-        else:
-            lat = self.prep.get(req)
+        elif req.kind == "opt" and d in self.offloaded:
+            # the design's state was moved to host memory: bring it back
+            lat, gamma_h, sens, state = self.offloaded.pop(d)
+            self.host_used -= state.numel()
             nb = footprint(lat, self.storage)
-            while self.used + nb > self.budget:
-                if not self._evict_one():
-                    return False
+            if not self._make_room(nb):
+                self.offloaded[d] = (lat, gamma_h, sens, state)
+                self.host_used += state.numel()
+                return False
+            s = Solver.from_lattice(lat, storage=self.storage, device=self.device)
+            s.import_state(state)
+            self.n_restored += 1
+            gamma = opt_step_gamma(lat, gamma_h.to(self.device), sens)
+            s.set_gamma(gamma)
+            self.resident[d] = (s, lat, gamma, sens, nb)
+            self.used += nb
+            warm = True
+            self.prep.drop(req)
+        else:
+            nb = footprint_of(req, self.storage)
+            if not self._make_room(nb):
+                return False
+            lat = self.prep.get(req)
             s = Solver.from_lattice(lat, storage=self.storage, device=self.device)
             gamma = torch.as_tensor(lat.gamma, dtype=s.rdtype, device=self.device)
             if req.kind == "opt":
-                # design not resident any more: replay its update from a cold state
+                # no state of the design is kept any more: replay its update cold
                 gamma = gamma.clone()
             if d in self.resident:
                 old = self.resident.pop(d)
                 old[0].close()
                 self.used -= old[4]
+            self.offloaded.pop(d, None)
             self.resident[d] = (s, lat, gamma, None, nb)
             self.used += nb
         self.batch.admit(s, self.tol, self.max_steps, reset=not warm)
@@ -335,6 +382,8 @@ class Server:
 
     def close(self):
         self.prep.close()
+        self.offloaded.clear()
+        self.host_used = 0
         for d in list(self.resident):
             self.resident.pop(d)[0].close()
         self.batch.close()

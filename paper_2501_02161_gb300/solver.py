@@ -177,6 +177,30 @@ class Solver:
                                          dt, 1), "lbm_get_adjoint")
         return fs, gs
 
+    # ---- checkpoint / resume ------------------------------------------------
+    def state_bytes(self) -> int:
+        return int(self.lib.lbm_state_bytes(self._ctx))
+
+    def export_state(self, out: torch.Tensor | None = None, pin: bool = True) -> torch.Tensor:
+        """The solver state as a uint8 tensor (host memory, pinned by default,
+        unless `out` is given: any device, at least state_bytes() long)."""
+        nb = self.state_bytes()
+        if out is None:
+            out = torch.empty(nb, dtype=torch.uint8, pin_memory=pin)
+        assert out.dtype == torch.uint8 and out.is_contiguous() and out.numel() >= nb
+        self._stream()
+        C.check(self.lib.lbm_export_state(self._ctx, ctypes.c_void_p(out.data_ptr()), nb),
+                "lbm_export_state")
+        return out
+
+    def import_state(self, state: torch.Tensor):
+        """Continue from a state written by export_state (same lattice, flags and
+        parameters set; gamma may differ)."""
+        assert state.dtype == torch.uint8 and state.is_contiguous()
+        self._stream()
+        C.check(self.lib.lbm_import_state(self._ctx, ctypes.c_void_p(state.data_ptr()),
+                                          state.numel()), "lbm_import_state")
+
     def time_steps(self, phase: int, n: int) -> float:
         """Mean ms per plain fused step of a phase (0 flow, 1 temperature,
         2 flow adjoint, 3 temperature adjoint), CUDA events on its stream."""

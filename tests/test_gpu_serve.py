@@ -122,3 +122,25 @@ def test_server_matches_sequential_bitwise():
         if a.status >= 0:
             assert a.steps == b.steps, (a.rid, a.steps, b.steps)
             assert torch.equal(a.sens.cpu(), b.sens.cpu()), a.rid
+
+
+def test_tight_budget_offloads_designs_and_still_matches_sequential():
+    """With room for about two lattices the server evicts designs; finished
+    ones move to host memory (lbm_export_state) and come back for their
+    optimisation steps (lbm_import_state), so every result, warm starts
+    included, is bit-identical to the baseline that keeps all designs."""
+    from paper_2501_02161_gb300.serve import Server, footprint, lattice_for, serve_sequential
+    reqs = _reqs()
+    biggest = max(footprint(lattice_for(r), "fp32") for r in reqs)
+    srv = Server("fp32", budget_bytes=int(2.5 * biggest), check_every=K, max_slots=8,
+                 tol=1e-5, max_steps=20000)
+    served = srv.run(reqs, realtime=False)
+    restored = srv.n_restored
+    srv.close()
+    seq = serve_sequential(reqs, "fp32", tol=1e-5, max_steps=20000, check_every=K, realtime=False)
+    assert restored >= 1
+    for a, b in zip(served, seq):
+        assert (a.status, a.warm) == (b.status, b.warm), (a.rid, a.status, b.status)
+        if a.status >= 0:
+            assert a.steps == b.steps, (a.rid, a.steps, b.steps)
+            assert torch.equal(a.sens.cpu(), b.sens.cpu()), a.rid
