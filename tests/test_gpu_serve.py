@@ -144,3 +144,54 @@ def test_tight_budget_offloads_designs_and_still_matches_sequential():
         if a.status >= 0:
             assert a.steps == b.steps, (a.rid, a.steps, b.steps)
             assert torch.equal(a.sens.cpu(), b.sens.cpu()), a.rid
+
+
+@pytest.mark.parametrize("solo_tiles", [None, 0], ids=["solo", "packed"])
+def test_largest_served_shape_matches_oracle(solo_tiles):
+    """The largest served lattice (192 x 96 x 48 heat sink, flow + temperature)
+    through the batch, on its own graph (solo, the default at this size) and
+    inside the packed persistent launch, against the FP64 oracle after the same
+    fixed number of steps of every phase: every node compared, FP32 tolerances
+    (rel-L2 1e-5 on rho, u, T, J; 1e-4 on f*, g*, dJ/dgamma)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2501_02161_gb300.serve import Batch
+    from paper_2501_02161_gb300.solver import Solver
+    O.build()
+    n = 20
+    lat = I.heat_sink(nx=192, ny=96, nz=48, re=50.0, seed=4)
+    b = Batch("fp32", 10, 4, solo_tiles)
+    s = Solver.from_lattice(lat, storage="fp32")
+    b.admit(s, 0.0, n, reset=True)
+    reps = []
+    while not reps:
+        b.step()
+        reps = b.poll()
+    assert reps[0][2].status == 0 and reps[0][2].steps == 4 * n
+    rho, u, T = s.fields(torch.float64)
+    fs, gs = s.adjoint_fields(torch.float64)
+    g = dict(rho=rho.cpu().numpy(), u=u.cpu().numpy().T, T=T.cpu().numpy(),
+             sens=s.sensitivity(dtype=torch.float64).cpu().numpy(),
+             fs=fs.cpu().numpy().T, gs=gs.cpu().numpy().T)
+    s.close()
+    b.close()
+
+    orc = O.Oracle(lat)
+    orc.flow_run(n)
+    orc.thermal_run(n)
+    o = {"T": orc.temperature()}
+    orc.thermal_adjoint_run(n)
+    orc.finish_thermal_adjoint()
+    o["gs"] = orc.thermal_adjoint_post_bc().reshape(orc.N, 7)
+    orc.adjoint_run(n)
+    o["rho"], o["u"] = orc.macro()
+    o.update(sens=orc.sensitivity(), fs=orc.adjoint_post_bc().reshape(orc.N, orc.Q))
+
+    def rel(a, c):
+        a, c = np.asarray(a, float), np.asarray(c, float)
+        return np.linalg.norm(a - c) / max(np.linalg.norm(c), 1e-300)
+    errs = {k: rel(g[k], o[k]) for k in g}
+    for k in ("rho", "u", "T"):
+        assert errs[k] <= 1e-5, errs
+    for k in ("sens", "fs", "gs"):
+        assert errs[k] <= 1e-4, errs
