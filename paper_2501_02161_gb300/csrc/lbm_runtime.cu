@@ -544,12 +544,15 @@ lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_devi
     }
     CUDA_TRY(cudaMemcpyAsync(c->flags, h.data(), n, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // the captured step graphs read the flags from device memory, but their
+    // objective source terms are baked from N_in and N_nonwall: recapture only
+    // when those counts change
+    if (!c->have_flags || nin != c->n_in || nnw != c->n_nw) c->drop_graphs();
     c->n_in = nin;
     c->n_nw = nnw;
     c->have_flags = true;
     c->fwd_done = c->adj_done = false;
     c->fstate = c->astate = false;
-    c->drop_graphs();  // objective source depends on N_in / N_nonwall
     return leave(c);
 }
 
@@ -588,19 +591,25 @@ lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
     if (c->thermal && !(p->kappa_f >= 0)) return fail(LBM_ERR_ARG, "kappa_f must be >= 0");
     if (c->thermal && !(p->k_ratio > 0)) return fail(LBM_ERR_ARG, "k_ratio must be > 0");
     if (!std::isfinite(p->q_flux) || !std::isfinite(p->T0)) return fail(LBM_ERR_ARG, "non-finite q_flux / T0");
+    // the captured graphs bake these values into their launches: recapture
+    // only when one of them changes
+    const lbm_params& q = c->prm;
+    const bool same = c->have_params && q.tau == p->tau && q.rho0 == p->rho0 &&
+                      q.gamma_model == p->gamma_model && q.kappa_f == p->kappa_f &&
+                      q.k_ratio == p->k_ratio && q.q_flux == p->q_flux && q.T0 == p->T0;
+    if (!same) c->drop_graphs();
     c->prm = *p;
     c->have_params = true;
     c->fwd_done = c->adj_done = false;
-    c->drop_graphs();
     return LBM_OK;
 }
 
 lbm_status lbm_set_objective(lbm_ctx* c, const lbm_objective* o) {
     if (!c || !o) return fail(LBM_ERR_ARG, "null argument");
     if (!std::isfinite(o->w_pin) || !std::isfinite(o->w_tmean)) return fail(LBM_ERR_ARG, "non-finite weights");
+    if (c->obj.w_pin != o->w_pin || c->obj.w_tmean != o->w_tmean) c->drop_graphs();
     c->obj = *o;
     c->adj_done = false;
-    c->drop_graphs();
     return LBM_OK;
 }
 

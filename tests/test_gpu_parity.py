@@ -166,6 +166,36 @@ def test_repeatable_and_warm_start_bitwise():
     assert torch.equal(a, b) and torch.equal(a, c)
 
 
+def test_new_inputs_on_a_used_context_match_a_fresh_context():
+    """Re-setting the same inputs keeps the captured step graphs and gives
+    bit-identical results; inputs with other inlet / non-wall node counts (and
+    other parameters) must behave exactly like a fresh context."""
+    from paper_2501_02161_gb300.solver import Solver
+
+    def solve(s):
+        rf = s.forward(tol=0, max_steps=200, check_every=100)
+        ra = s.adjoint(tol=0, max_steps=100, check_every=100)
+        return rf.J, ra.I, s.sensitivity(dtype=torch.float64).cpu()
+
+    a = I.pipe_bend_3d(n=24, width=6, re=30.0, seed=5)
+    b = I.pipe_bend_3d(n=24, width=4, re=15.0, seed=6)   # other N_in, N_nonwall, tau
+    s = Solver.from_lattice(a, storage="fp32")
+    first = solve(s)
+    for lat in (a, b, a):
+        s.set_flags(torch.as_tensor(lat.flags))
+        s.set_gamma(torch.as_tensor(lat.gamma, dtype=torch.float32))
+        s.set_bc_values(torch.as_tensor(lat.bcval, dtype=torch.float32))
+        s.set_params(tau=lat.tau, rho0=lat.rho0, gamma_model=lat.gamma_model)
+        s.set_objective(lat.w_pin, lat.w_tmean)
+        got = solve(s)
+        fresh = Solver.from_lattice(lat, storage="fp32")
+        ref = solve(fresh)
+        fresh.close()
+        assert got[0] == ref[0] and got[1] == ref[1] and torch.equal(got[2], ref[2]), lat.name
+    assert first[0] == got[0] and torch.equal(first[2], got[2])
+    s.close()
+
+
 def test_degenerate_periodic_box_stays_at_rest():
     """All-fluid periodic lattice with no boundaries: the rest state is a fixed point."""
     from paper_2501_02161_gb300.solver import Solver
