@@ -125,6 +125,52 @@ template <> struct Pop<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
+// rounding-explicit arithmetic.  The node functions are inlined into several
+// kernels (the single-lattice steps and the packed serving kernel).  Written
+// with these operations, every multiply, add and fused multiply-add is fixed
+// in the source: the compiler can neither fuse nor split them differently from
+// one kernel to the next, so a node rounds identically wherever it runs.
+// Coefficients that are lattice constants (components of e_i in {-1, 0, 1})
+// enter through compile-time branches, so no multiply by 0 or 1 is executed.
+// ---------------------------------------------------------------------------
+template <typename R> struct Ex;
+template <> struct Ex<float> {
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Ex<double> {
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+// a + s b for a sign s in {-1, 0, 1} known at compile time (s = 0 gives a)
+template <typename R>
+__device__ __forceinline__ R add_s(R a, int s, R b) {
+    return s > 0 ? Ex<R>::add(a, b) : (s < 0 ? Ex<R>::sub(a, b) : a);
+}
+
+// e.v for a direction e with components in {-1, 0, 1} known at compile time,
+// summed x, y, z in that order
+template <typename R>
+__device__ __forceinline__ R edot(int x, int y, int z, R v0, R v1, R v2) {
+    R r = R(0);
+    bool any = false;
+    if (x) { r = x > 0 ? v0 : -v0; any = true; }
+    if (y) { r = any ? add_s(r, y, v1) : (y > 0 ? v1 : -v1); any = true; }
+    if (z) { r = any ? add_s(r, z, v2) : (z > 0 ? v2 : -v2); }
+    return r;
+}
+
+template <class L, typename R>
+__device__ __forceinline__ R edot_i(int i, R v0, R v1, R v2) {
+    return edot<R>(L::cx(i), L::cy(i), L::cz(i), v0, v1, v2);
+}
+
+// ---------------------------------------------------------------------------
 // kernel arguments (passed by value)
 // ---------------------------------------------------------------------------
 template <typename T, typename TA, typename R>
@@ -270,6 +316,7 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* __restri
 // ---------------------------------------------------------------------------
 template <class L, typename R>
 __device__ __forceinline__ void zou_he(R (&f)[L::Q], int type, int code, const R* __restrict__ bc, R rho0) {
+    using X = Ex<R>;
     const int ax = code >> 1;
     const int sg = (code & 1) ? -1 : 1;
     const int n0 = ax == 0 ? sg : 0, n1 = ax == 1 ? sg : 0, n2 = ax == 2 ? sg : 0;
@@ -278,12 +325,12 @@ __device__ __forceinline__ void zou_he(R (&f)[L::Q], int type, int code, const R
     for (int i = 0; i < L::Q; ++i) {
         const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
         if (d == 0) {
-            K0 += f[i];
-            S0 += R(L::cx(i)) * f[i];
-            S1 += R(L::cy(i)) * f[i];
-            S2 += R(L::cz(i)) * f[i];
+            K0 = X::add(K0, f[i]);
+            S0 = add_s(S0, L::cx(i), f[i]);
+            S1 = add_s(S1, L::cy(i), f[i]);
+            S2 = add_s(S2, L::cz(i), f[i]);
         } else if (d < 0) {
-            Km += f[i];
+            Km = X::add(Km, f[i]);
         }
     }
     R u0, u1, u2;
@@ -293,24 +340,24 @@ __device__ __forceinline__ void zou_he(R (&f)[L::Q], int type, int code, const R
         u2 = bc[2];
     } else {
         // sums of offset populations: sum_{e.n=0} w + 2 sum_{e.n<0} w = 1
-        const R un = (bc[0] - rho0 - K0 - R(2) * Km) / rho0;
-        u0 = un * R(n0);
-        u1 = un * R(n1);
-        u2 = un * R(n2);
+        const R un = X::fma(R(-2), Km, X::sub(X::sub(bc[0], rho0), K0)) / rho0;
+        u0 = X::mul(un, R(n0));
+        u1 = X::mul(un, R(n1));
+        u2 = X::mul(un, R(n2));
     }
-    const R unn = u0 * R(n0) + u1 * R(n1) + u2 * R(n2);
-    const R t0 = u0 - unn * R(n0), t1 = u1 - unn * R(n1), t2 = u2 - unn * R(n2);
-    const R third = R(1) / R(3);
-    const R N0 = R(0.5) * S0 - rho0 * third * t0;
-    const R N1 = R(0.5) * S1 - rho0 * third * t1;
-    const R N2 = R(0.5) * S2 - rho0 * third * t2;
+    const R unn = X::fma(u2, R(n2), X::fma(u1, R(n1), X::mul(u0, R(n0))));
+    const R t0 = X::fma(-unn, R(n0), u0), t1 = X::fma(-unn, R(n1), u1), t2 = X::fma(-unn, R(n2), u2);
+    const R k3 = X::mul(rho0, R(1) / R(3));
+    const R N0 = X::fma(-k3, t0, X::mul(R(0.5), S0));
+    const R N1 = X::fma(-k3, t1, X::mul(R(0.5), S1));
+    const R N2 = X::fma(-k3, t2, X::mul(R(0.5), S2));
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
         if (d > 0) {
-            const R eu = R(L::cx(i)) * u0 + R(L::cy(i)) * u1 + R(L::cz(i)) * u2;
-            const R eN = R(L::cx(i)) * N0 + R(L::cy(i)) * N1 + R(L::cz(i)) * N2;
-            f[i] = f[L::opp(i)] + R(6.0 * L::w(i)) * rho0 * eu - eN;
+            const R eu = edot_i<L>(i, u0, u1, u2);
+            const R eN = edot_i<L>(i, N0, N1, N2);
+            f[i] = X::sub(X::fma(X::mul(R(6.0 * L::w(i)), rho0), eu, f[L::opp(i)]), eN);
         }
     }
 }
@@ -323,6 +370,7 @@ __device__ __forceinline__ void zou_he(R (&f)[L::Q], int type, int code, const R
 // Eq. 59 (left velocity inlet) and Eq. 60 (bottom fixed-density outlet).
 template <class L, typename R>
 __device__ __forceinline__ void zou_he_adjoint(R (&c)[L::Q], int type, int code) {
+    using X = Ex<R>;
     const int ax = code >> 1;
     const int sg = (code & 1) ? -1 : 1;
     const int n0 = ax == 0 ? sg : 0, n1 = ax == 1 ? sg : 0, n2 = ax == 2 ? sg : 0;
@@ -331,10 +379,10 @@ __device__ __forceinline__ void zou_he_adjoint(R (&c)[L::Q], int type, int code)
     for (int i = 0; i < L::Q; ++i) {
         const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
         if (d > 0) {
-            M0 += R(L::cx(i)) * c[i];
-            M1 += R(L::cy(i)) * c[i];
-            M2 += R(L::cz(i)) * c[i];
-            P += R(6.0 * L::w(i)) * c[i];
+            M0 = add_s(M0, L::cx(i), c[i]);
+            M1 = add_s(M1, L::cy(i), c[i]);
+            M2 = add_s(M2, L::cz(i), c[i]);
+            P = X::fma(R(6.0 * L::w(i)), c[i], P);
         }
     }
     if (type != PRES) P = R(0);
@@ -343,9 +391,9 @@ __device__ __forceinline__ void zou_he_adjoint(R (&c)[L::Q], int type, int code)
     for (int i = 0; i < L::Q; ++i) {
         const int d = L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2;
         if (d < 0)
-            c[i] = c[i] + c[L::opp(i)] - R(2) * P;
+            c[i] = X::fma(R(-2), P, X::add(c[i], c[L::opp(i)]));
         else if (d == 0)
-            c[i] = c[i] - R(0.5) * (R(L::cx(i)) * M0 + R(L::cy(i)) * M1 + R(L::cz(i)) * M2) - P;
+            c[i] = X::sub(X::fma(R(-0.5), edot_i<L>(i, M0, M1, M2), c[i]), P);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -385,19 +433,20 @@ __device__ __forceinline__ int pull_forward(const FlowArgs<T, TA, R>& a, const C
 // drho = rho - rho0 = sum h, u = sum e h / rho0
 template <class L, typename R>
 __device__ __forceinline__ void moments(const R (&f)[L::Q], R rho0, R& rho, R& u0, R& u1, R& u2) {
+    using X = Ex<R>;
     R r = 0, j0 = 0, j1 = 0, j2 = 0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        r += f[i];
-        if (L::cx(i)) j0 += R(L::cx(i)) * f[i];
-        if (L::cy(i)) j1 += R(L::cy(i)) * f[i];
-        if (L::cz(i)) j2 += R(L::cz(i)) * f[i];
+        r = X::add(r, f[i]);
+        j0 = add_s(j0, L::cx(i), f[i]);
+        j1 = add_s(j1, L::cy(i), f[i]);
+        j2 = add_s(j2, L::cz(i), f[i]);
     }
     const R inv = R(1) / rho0;
     rho = r;
-    u0 = j0 * inv;
-    u1 = j1 * inv;
-    u2 = j2 * inv;
+    u0 = X::mul(j0, inv);
+    u1 = X::mul(j1, inv);
+    u2 = X::mul(j2, inv);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,43 +459,44 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
     const int type = fl & 7;
     R drho, u0, u1, u2;
     moments<L>(f, a.rho0, drho, u0, u1, u2);
+    using X = Ex<R>;
     if (REDUCE) {  // the fields and the frozen velocity of this post-boundary state
-        a.out0[c.n] = a.rho0 + drho;
+        a.out0[c.n] = X::add(a.rho0, drho);
         a.out1[c.n] = u0;
         a.out1[a.np + c.n] = u1;
         a.out1[2 * a.np + c.n] = u2;
     }
     if (type != WALL) {
         if (REDUCE) {
-            acc[0] = (double)sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-            if (type == VEL) acc[1] = (double)(a.rho0 + drho);
+            acc[0] = (double)sqrt(X::fma(u2, u2, X::fma(u1, u1, X::mul(u0, u0))));
+            if (type == VEL) acc[1] = (double)X::add(a.rho0, drho);
         }
         const R g = a.gamma[c.n];
         R a0, a1, a2, amp;
         if (a.model == 0) {
-            a0 = g * u0; a1 = g * u1; a2 = g * u2; amp = R(1);
+            a0 = X::mul(g, u0); a1 = X::mul(g, u1); a2 = X::mul(g, u2); amp = R(1);
         } else {
             a0 = u0; a1 = u1; a2 = u2; amp = g;
         }
-        const R uu = a0 * a0 + a1 * a1 + a2 * a2;
-        const R om = a.omega, om1 = R(1) - om;
+        const R uu = X::fma(a2, a2, X::fma(a1, a1, X::mul(a0, a0)));
+        const R om = a.omega, om1 = X::sub(R(1), om);
         // h_eq,i = w_i (drho + k (3 e_i.a + 4.5 (e_i.a)^2 - 1.5 a.a)), k = rho0 amp.
         // A direction and its opposite share the even part and negate the odd
         // one, so each pair is evaluated once; 1/tau is folded into w_i.
-        const R k = a.rho0 * amp;
-        const R ev = drho - R(1.5) * k * uu;
-        const R k45 = R(4.5) * k, k3 = R(3) * k;
-        f[0] = om1 * f[0] + (om * R(L::w(0))) * ev;
+        const R k = X::mul(a.rho0, amp);
+        const R ev = X::fma(-X::mul(R(1.5), k), uu, drho);
+        const R k45 = X::mul(R(4.5), k), k3 = X::mul(R(3), k);
+        f[0] = X::fma(om1, f[0], X::mul(X::mul(om, R(L::w(0))), ev));
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
             if (L::opp(i) < i) continue;
             const int j = L::opp(i);
-            const R omw = om * R(L::w(i));
-            const R eu = R(L::cx(i)) * a0 + R(L::cy(i)) * a1 + R(L::cz(i)) * a2;
-            const R even = omw * (ev + k45 * eu * eu);
-            const R odd = (omw * k3) * eu;
-            f[i] = om1 * f[i] + (even + odd);
-            f[j] = om1 * f[j] + (even - odd);
+            const R omw = X::mul(om, R(L::w(i)));
+            const R eu = edot_i<L>(i, a0, a1, a2);
+            const R even = X::mul(omw, X::fma(X::mul(k45, eu), eu, ev));
+            const R odd = X::mul(X::mul(omw, k3), eu);
+            f[i] = X::fma(om1, f[i], X::add(even, odd));
+            f[j] = X::fma(om1, f[j], X::sub(even, odd));
         }
     }
 #pragma unroll
@@ -494,22 +544,23 @@ struct AdjMoments {
     // a direction and its opposite enter A and Q through their sum and M
     // through their difference (e_opp = -e), so each pair is read once
     __device__ __forceinline__ void compute(const R (&s)[L::Q]) {
+        using X = Ex<R>;
         M0 = M1 = M2 = Q00 = Q11 = Q22 = Q01 = Q02 = Q12 = R(0);
-        A = R(L::w(0)) * s[0];
+        A = X::mul(R(L::w(0)), s[0]);
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
             if (L::opp(i) < i) continue;
             const int j = L::opp(i);
-            const R wp = R(L::w(i)) * (s[i] + s[j]);
-            const R wd = R(L::w(i)) * (s[i] - s[j]);
+            const R wp = X::mul(R(L::w(i)), X::add(s[i], s[j]));
+            const R wd = X::mul(R(L::w(i)), X::sub(s[i], s[j]));
             const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-            A += wp;
-            if (x) { M0 += R(x) * wd; Q00 += wp; }
-            if (y) { M1 += R(y) * wd; Q11 += wp; }
-            if (z) { M2 += R(z) * wd; Q22 += wp; }
-            if (x * y) Q01 += R(x * y) * wp;
-            if (x * z) Q02 += R(x * z) * wp;
-            if (y * z) Q12 += R(y * z) * wp;
+            A = X::add(A, wp);
+            if (x) { M0 = add_s(M0, x, wd); Q00 = X::add(Q00, wp); }
+            if (y) { M1 = add_s(M1, y, wd); Q11 = X::add(Q11, wp); }
+            if (z) { M2 = add_s(M2, z, wd); Q22 = X::add(Q22, wp); }
+            Q01 = add_s(Q01, x * y, wp);
+            Q02 = add_s(Q02, x * z, wp);
+            Q12 = add_s(Q12, y * z, wp);
         }
     }
 };
@@ -543,40 +594,45 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
     if (type == WALL) {
         bounce<L>(s);  // C^T = I, B^T = the same swap
     } else {
+        using X = Ex<R>;
         const R g = a.gamma[c.n];
         const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
         AdjMoments<L, R> m;
         m.compute(s);
-        const R Qu0 = m.Q00 * u0 + m.Q01 * u1 + m.Q02 * u2;
-        const R Qu1 = m.Q01 * u0 + m.Q11 * u1 + m.Q12 * u2;
-        const R Qu2 = m.Q02 * u0 + m.Q12 * u1 + m.Q22 * u2;
+        const R Qu0 = X::fma(m.Q02, u2, X::fma(m.Q01, u1, X::mul(m.Q00, u0)));
+        const R Qu1 = X::fma(m.Q12, u2, X::fma(m.Q11, u1, X::mul(m.Q01, u0)));
+        const R Qu2 = X::fma(m.Q22, u2, X::fma(m.Q12, u1, X::mul(m.Q02, u0)));
         // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
-        const R c1 = R(3) * g;
-        const R c2 = a.model == 0 ? R(9) * g * g : R(9) * g;
-        const R c3 = a.model == 0 ? R(3) * g * g : R(3) * g;
-        R w0 = c1 * m.M0 + c2 * Qu0 - c3 * m.A * u0;
-        R w1 = c1 * m.M1 + c2 * Qu1 - c3 * m.A * u1;
-        R w2 = c1 * m.M2 + c2 * Qu2 - c3 * m.A * u2;
+        const R c1 = X::mul(R(3), g);
+        const R c2 = a.model == 0 ? X::mul(X::mul(R(9), g), g) : X::mul(R(9), g);
+        const R c3 = a.model == 0 ? X::mul(c1, g) : c1;
+        const R c3A = X::mul(c3, m.A);
+        R w0 = X::fma(-c3A, u0, X::fma(c2, Qu0, X::mul(c1, m.M0)));
+        R w1 = X::fma(-c3A, u1, X::fma(c2, Qu1, X::mul(c1, m.M1)));
+        R w2 = X::fma(-c3A, u2, X::fma(c2, Qu2, X::mul(c1, m.M2)));
         const R om = a.omega;
-        const R base = om * m.A - (type == VEL ? a.src_in : R(0));
+        R base = X::mul(om, m.A);
+        if (type == VEL) base = X::sub(base, a.src_in);
+        // the coupling term enters through the same fused operation whether
+        // it is present or zero, so every kernel variant rounds alike
         R v0 = 0, v1 = 0, v2 = 0;
         if (THERMAL || (CPL_RT && a.cpl != nullptr)) {
             v0 = a.cpl[c.n];
             v1 = a.cpl[a.np + c.n];
             v2 = a.cpl[2 * a.np + c.n];
         }
-        w0 = om * w0 + v0;
-        w1 = om * w1 + v1;
-        w2 = om * w2 + v2;
-        const R om1 = R(1) - om;
-        s[0] = om1 * s[0] + base;
+        w0 = X::fma(om, w0, v0);
+        w1 = X::fma(om, w1, v1);
+        w2 = X::fma(om, w2, v2);
+        const R om1 = X::sub(R(1), om);
+        s[0] = X::fma(om1, s[0], base);
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
             if (L::opp(i) < i) continue;
             const int j = L::opp(i);
-            const R ew = R(L::cx(i)) * w0 + R(L::cy(i)) * w1 + R(L::cz(i)) * w2;
-            s[i] = om1 * s[i] + (base + ew);
-            s[j] = om1 * s[j] + (base - ew);
+            const R ew = edot_i<L>(i, w0, w1, w2);
+            s[i] = X::fma(om1, s[i], X::add(base, ew));
+            s[j] = X::fma(om1, s[j], X::sub(base, ew));
         }
         if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
     }
@@ -586,7 +642,7 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
     if (REDUCE && type != WALL) {
         R t = 0;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) t += fabs(s[i]);
+        for (int i = 0; i < L::Q; ++i) t = Ex<R>::add(t, fabs(s[i]));
         acc[0] = (double)t;
     }
 }
@@ -638,12 +694,13 @@ __global__ void __launch_bounds__(256) k_flow_sens(FlowArgs<T, TA, R> a) {
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R tau_g(R g, R kappa_f, R k_ratio) {
-    return R(0.5) + R(4) * kappa_f * (g + (R(1) - g) * k_ratio);
+    using X = Ex<R>;
+    return X::fma(X::mul(R(4), kappa_f), X::fma(X::sub(R(1), g), k_ratio, g), R(0.5));
 }
 
 template <typename R>
 __device__ __forceinline__ R ecomp(int k, R u0, R u1, R u2) {  // e_k . u for D3Q7
-    return R(D3Q7::cx(k)) * u0 + R(D3Q7::cy(k)) * u1 + R(D3Q7::cz(k)) * u2;
+    return edot<R>(D3Q7::cx(k), D3Q7::cy(k), D3Q7::cz(k), u0, u1, u2);
 }
 
 // thermal boundary operator: wall bounce-back (+ heat flux), Dirichlet inlet,
@@ -659,24 +716,25 @@ __device__ __forceinline__ void thermal_bc(R (&g)[7], int fl, const R* __restric
         if (fl & HEAT_BIT) {
 #pragma unroll
             for (int k = 1; k < 7; ++k)
-                if (k == kn) g[k] += q;
+                if (k == kn) g[k] = Ex<R>::add(g[k], q);
         }
         return;
     }
+    using X = Ex<R>;
     R K = 0;
 #pragma unroll
     for (int k = 0; k < 7; ++k)
-        if (k != kn) K += g[k];
+        if (k != kn) K = X::add(K, g[k]);
     R val;
     if (type == VEL) {
-        val = bc[3] - K;
+        val = X::sub(bc[3], K);
     } else {
         R en = 0;
 #pragma unroll
         for (int k = 1; k < 7; ++k)
             if (k == kn) en = ecomp<R>(k, u0, u1, u2);
-        const R wa = R(0.125) * (R(1) + R(4) * gam * en);
-        val = wa * K / (R(1) - wa);
+        const R wa = X::mul(R(0.125), X::fma(X::mul(R(4), gam), en, R(1)));
+        val = X::mul(wa, K) / X::sub(R(1), wa);
     }
 #pragma unroll
     for (int k = 1; k < 7; ++k)
@@ -704,9 +762,10 @@ template <typename T, typename TA, typename R, bool REDUCE>
 __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
     R g[7], gam, u0, u1, u2;
     const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
+    using X = Ex<R>;
     R tem = 0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) tem += g[k];
+    for (int k = 0; k < 7; ++k) tem = X::add(tem, g[k]);
     if (REDUCE) {  // temperature and frozen post-boundary g of this state
         a.out0[c.n] = tem;
 #pragma unroll
@@ -715,11 +774,11 @@ __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, 
     if ((fl & 7) != WALL) {
         if (REDUCE) acc[0] = (double)tem;
         const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
-        const R g4 = R(4) * gam;
+        const R g4 = X::mul(R(4), gam);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            const R geq = R(D3Q7::w(k)) * tem * (R(1) + g4 * ecomp<R>(k, u0, u1, u2));
-            g[k] += om * (geq - g[k]);
+            const R geq = X::mul(X::mul(R(D3Q7::w(k)), tem), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1)));
+            g[k] = X::fma(om, X::sub(geq, g[k]), g[k]);
         }
     }
 #pragma unroll
@@ -761,13 +820,16 @@ __global__ void k_thermal_init(ThermArgs<T, TA, R> a, int which) {
 //   g*_C,l = (1 - 1/tau_g) g*_S,l + (1/tau_g) sum_k w_k a_k g*_S,k - dJ/dg_l
 template <typename R>
 __device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, R u1, R u2, R om, R src) {
+    using X = Ex<R>;
     R B = 0;
-    const R g4 = R(4) * gam;
+    const R g4 = X::mul(R(4), gam);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) B += R(D3Q7::w(k)) * (R(1) + g4 * ecomp<R>(k, u0, u1, u2)) * s[k];
-    const R base = om * B - src;
+    for (int k = 0; k < 7; ++k)
+        B = X::fma(X::mul(R(D3Q7::w(k)), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1))), s[k], B);
+    const R base = X::fma(om, B, -src);
+    const R om1 = X::sub(R(1), om);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) s[k] = (R(1) - om) * s[k] + base;
+    for (int k = 0; k < 7; ++k) s[k] = X::fma(om1, s[k], base);
 }
 
 template <typename T, typename TA, typename R>
@@ -804,12 +866,12 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
             if (type == VEL) {
                 coef = R(-1);
             } else {
-                const R wa = R(0.125) * (R(1) + R(4) * gam * en);
-                coef = wa / (R(1) - wa);
+                const R wa = Ex<R>::mul(R(0.125), Ex<R>::fma(Ex<R>::mul(R(4), gam), en, R(1)));
+                coef = wa / Ex<R>::sub(R(1), wa);
                 a.gcn[c.n] = ckn;
             }
 #pragma unroll
-            for (int k = 0; k < 7; ++k) s[k] = (k == kn) ? R(0) : s[k] + coef * ckn;
+            for (int k = 0; k < 7; ++k) s[k] = (k == kn) ? R(0) : Ex<R>::fma(coef, ckn, s[k]);
         }
     }
     const R inv = R(1) / a.ascale;
@@ -818,7 +880,7 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
     if (REDUCE && type != WALL) {
         R t = 0;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) t += fabs(s[k]);
+        for (int k = 0; k < 7; ++k) t = Ex<R>::add(t, fabs(s[k]));
         acc[0] = (double)t;
     }
 }
