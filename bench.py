@@ -39,7 +39,7 @@ THERM_BYTES = 7 * 4 * 2 + 12 + 4 + 1   # D3Q7 FP32 populations + frozen u + gamm
 # / nodes) from one ncu capture of the current kernels on a 160^3 pipe bend
 # (profiles/k_flow_*_pipe_bend_160cubed_fp32.md); traffic grows with the node
 # count, so a launch on N nodes moves N times this.
-TRAFFIC_B_PER_NODE = {("adjoint", "fp32"): 156.8, ("forward", "fp32"): 145.5}
+TRAFFIC_B_PER_NODE = {("adjoint", "fp32"): 156.8, ("forward", "fp32"): 145.4}
 
 
 def parse():
