@@ -371,7 +371,8 @@ class Server:
                     res.sens = sens
                     ent = self.resident[d]
                     self.resident[d] = (ent[0], ent[1], ent[2], sens, ent[4])
-                torch.cuda.synchronize(self.device)
+                if self.device.type == "cuda":
+                    torch.cuda.synchronize(self.device)
                 res.done = time.perf_counter() - t0
                 done += 1
                 if not self.keep or rep.status < 0:

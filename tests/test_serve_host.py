@@ -1,0 +1,195 @@
+"""Host-side scheduling of the serving loop, on CPU.
+
+The server's decisions (admission in arrival order, the slot and in-flight
+node caps, one request per design at a time, HBM-budget eviction with the
+design state moved to host memory and brought back) are plain Python; here
+they run against stand-ins for the solver and the batch, so every rule is
+checked without a GPU.  The GPU tests check the numbers; these check the
+schedule.
+"""
+import ctypes
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2501_02161_gb300 import serve as S
+from paper_2501_02161_gb300.solver import Report
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    from paper_2501_02161_gb300 import build as B
+    B.build()  # lbm_footprint_bytes is a host function of the library
+
+
+class FakeSolver:
+    _ids = itertools.count(1)
+    live = {}
+
+    def __init__(self, lat):
+        self.lat = lat
+        self.N = lat.n
+        self.rdtype = torch.float32
+        self._ctx = ctypes.c_void_p(next(FakeSolver._ids))
+        self.gamma = None
+        self.imported = None
+        FakeSolver.live[self._ctx.value] = self
+
+    @classmethod
+    def from_lattice(cls, lat, storage="fp32", device=None):
+        return cls(lat)
+
+    def set_gamma(self, g):
+        self.gamma = g
+
+    def sensitivity(self, dtype=None):
+        return torch.full((self.N,), float(self._ctx.value), dtype=dtype or torch.float32)
+
+    def export_state(self):
+        return torch.full((64,), self._ctx.value % 251, dtype=torch.uint8)
+
+    def import_state(self, st):
+        self.imported = st
+
+    def close(self):
+        FakeSolver.live.pop(self._ctx.value, None)
+
+
+class FakeBatch:
+    """Completes a context after a number of steps proportional to its nodes
+    (one step per 32^3 worth of nodes); records what ran together."""
+    instances = []
+
+    def __init__(self, storage, check_every, max_slots, solo_tiles=None):
+        self.active = {}
+        self.log = []
+        self.done = []
+        FakeBatch.instances.append(self)
+
+    def admit(self, solver, tol, max_steps, reset):
+        self.active[solver._ctx.value] = [solver, max(1, solver.N // 32768), reset]
+        return 0
+
+    def step(self):
+        self.log.append(sorted(self.active))
+        for ctx in list(self.active):
+            self.active[ctx][1] -= 1
+            if self.active[ctx][1] <= 0:
+                self.done.append(ctx)
+                del self.active[ctx]
+        return len(self.active)
+
+    def poll(self):
+        out = [(0, ctx, Report(10, 0.0, 0.0, 1.0, 0.0, 0)) for ctx in self.done]
+        self.done = []
+        return out
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def fakes(monkeypatch):
+    FakeSolver.live.clear()
+    FakeBatch.instances.clear()
+    monkeypatch.setattr(S, "Solver", FakeSolver)
+    monkeypatch.setattr(S, "Batch", FakeBatch)
+    return FakeBatch.instances
+
+
+def _reqs(n=24, seed=3):
+    return S.make_requests(n, seed=seed, rate=None, shapes=[(32, 32, 32), (64, 64, 64), (96, 48, 24)],
+                           re_range=(10.0, 60.0))
+
+
+def test_footprint_of_a_request_matches_its_lattice():
+    for r in _reqs(12):
+        assert S.footprint_of(r, "fp32") == S.footprint(S.lattice_for(r), "fp32")
+        assert S.footprint_of(r, "fp16") == S.footprint(S.lattice_for(r), "fp16")
+
+
+def test_lattice_prefetch_gives_the_same_lattices():
+    reqs = _reqs(6)
+    prep = S.LatticePrep(workers=2, ahead=4)
+    prep.want(reqs)
+    for r in reqs:
+        a, b = prep.get(r), S.lattice_for(r)
+        assert np.array_equal(a.flags, b.flags) and np.array_equal(a.gamma, b.gamma)
+        assert np.array_equal(a.bcval, b.bcval) and a.tau == b.tau
+    prep.close()
+
+
+def test_schedule_respects_slots_node_cap_and_design_order(fakes):
+    reqs = _reqs()
+    srv = S.Server("fp32", budget_bytes=1 << 60, check_every=500, max_slots=3,
+                   max_active_nodes=400_000, device="cpu")
+    res = srv.run(reqs, realtime=False)
+    log = fakes[0].log
+    srv.close()
+    assert all(r.status == 0 and r.done >= r.admitted for r in res)
+    assert max(len(step) for step in log) <= 3   # slots
+    assert max(len(step) for step in log) >= 2   # lattices did share the GPU
+    # one request per design at a time, and in arrival order per design
+    order = {}
+    for r in sorted(res, key=lambda r: r.admitted):
+        order.setdefault(reqs[r.rid].design, []).append(r)
+    for d, rs in order.items():
+        for a, b in zip(rs, rs[1:]):
+            assert a.done <= b.admitted and a.rid < b.rid
+    # optimisation steps on a finished design warm-start
+    assert any(r.kind == "opt" and r.warm for r in res)
+
+
+def test_node_cap_bounds_the_in_flight_nodes(fakes):
+    reqs = _reqs()
+    cap = 400_000
+    srv = S.Server("fp32", budget_bytes=1 << 60, check_every=500, max_slots=8,
+                   max_active_nodes=cap, device="cpu")
+    seen = []
+    orig = srv.batch.step
+
+    def step():
+        seen.append(srv._active_nodes())
+        return orig()
+    srv.batch.step = step
+    srv.run(reqs, realtime=False)
+    srv.close()
+    biggest = max(int(np.prod(r.shape)) for r in reqs)
+    assert max(seen) <= max(cap, biggest)
+
+
+def test_tight_budget_moves_designs_to_host_and_back(fakes):
+    reqs = _reqs(30, seed=4)
+    biggest = max(S.footprint_of(r, "fp32") for r in reqs)
+    srv = S.Server("fp32", budget_bytes=int(1.5 * biggest), check_every=500, max_slots=4,
+                   device="cpu")
+    peak = []
+    orig = srv.batch.step
+
+    def step():
+        peak.append(srv.used)
+        return orig()
+    srv.batch.step = step
+    res = srv.run(reqs, realtime=False)
+    restored = srv.n_restored
+    srv.close()
+    assert max(peak) <= 1.5 * biggest
+    assert all(r.status == 0 for r in res)
+    warm_opt = [r for r in res if r.kind == "opt" and r.warm]
+    assert restored >= 1 and len(warm_opt) >= restored
+    assert not FakeSolver.live  # every context was closed
+
+
+def test_host_budget_drops_the_oldest_offloaded_state(fakes):
+    reqs = _reqs(30, seed=4)
+    biggest = max(S.footprint_of(r, "fp32") for r in reqs)
+    srv = S.Server("fp32", budget_bytes=int(1.5 * biggest), check_every=500, max_slots=4,
+                   device="cpu", host_budget_bytes=64)  # room for one fake state
+    res = srv.run(reqs, realtime=False)
+    held = len(srv.offloaded)
+    srv.close()
+    assert held <= 1
+    assert all(r.status == 0 for r in res)
