@@ -19,6 +19,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbmadj.h"
 #include "lbm_internal.h"
 
@@ -271,8 +273,20 @@ double rel_change(double cur, double prev) {
 }
 
 // run a phase to tolerance (or a fixed number of steps when tol <= 0)
+// NVTX ranges name each solve phase and batch step on a profiler's timeline
+// (ncu --nvtx, Nsight Systems); with no tool attached a push/pop costs a call
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 lbm_status run_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, long long* steps_out,
                      double* res_out, double* I_out) {
+    static const char* const kPhaseNames[4] = {"lbm flow", "lbm temperature", "lbm flow adjoint",
+                                               "lbm temperature adjoint"};
+    NvtxRange range(kPhaseNames[ph & 3]);
     const int K = o->check_every;
     long long steps = 0;
     double res = INFINITY;
@@ -1223,6 +1237,7 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* c, const lbm_solve_opts* o, in
 
 lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
     if (!b) return fail(LBM_ERR_ARG, "batch is null");
+    NvtxRange range("lbm batch step");
     CUDA_TRY(cudaSetDevice(b->device));
     // contexts whose phase has nothing to do (max_steps reached) move on first
     for (int i = 0; i < b->max_slots; ++i) {
