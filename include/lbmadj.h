@@ -328,6 +328,16 @@ lbm_status lbm_flow_step_noalloc(const lbm_step_desc* d, void* cuda_stream);
 const char* lbm_last_error(void);
 
 /* Library version string. */
+/* Host-side check of the kernels' pull addressing (no counterpart in the
+ * paper; a stand-in for a memory checker, which this GPU pool does not run).
+ * Runs, on the CPU and without a GPU, the same neighbour-offset code the
+ * kernels use for every node and every direction e_i, both ways (x - e_i for
+ * the forward pull, x + e_i for the adjoint pull), and stores in *mismatches
+ * how many computed sources differ from the periodic wrap of x -/+ e_i or fall
+ * outside the lattice.  stencil: 0 D2Q9, 1 D3Q19, 2 D3Q7 (temperature).
+ * Errors: LBM_ERR_ARG (null pointer, bad sizes, more than 2^24 nodes). */
+lbm_status lbm_check_addressing(int stencil, int nx, int ny, int nz, long long* mismatches);
+
 const char* lbm_version(void);
 
 #ifdef __cplusplus

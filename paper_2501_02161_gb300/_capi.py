@@ -86,6 +86,7 @@ SIGNATURES = {
     "lbm_batch_set_solo_tiles": (_I, [_VP, ctypes.c_longlong]),
     "lbm_batch_poll": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(lbm_report),
                             _I, ctypes.POINTER(_I)]),
+    "lbm_check_addressing": (_I, [_I, _I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_version": (ctypes.c_char_p, []),
 }

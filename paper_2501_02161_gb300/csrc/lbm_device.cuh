@@ -245,7 +245,7 @@ struct Nbr {
     int xm, xp, ym, yp, zm, zp;
 };
 
-__device__ __forceinline__ Nbr neighbours(const Cell& c, int nx, int ny, int nz) {
+__host__ __device__ __forceinline__ Nbr neighbours(const Cell& c, int nx, int ny, int nz) {
     const int sy = nx, sz = nx * ny;
     Nbr o;
     o.xm = c.x == 0 ? nx - 1 : -1;
@@ -259,7 +259,7 @@ __device__ __forceinline__ Nbr neighbours(const Cell& c, int nx, int ny, int nz)
 
 // offset of x + s e_i (s = +1 or -1); the selections fold at compile time
 template <class L>
-__device__ __forceinline__ int nbr_offset(const Nbr& o, int i, int s) {
+__host__ __device__ __forceinline__ int nbr_offset(const Nbr& o, int i, int s) {
     const int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
     return (dx < 0 ? o.xm : (dx > 0 ? o.xp : 0)) + (dy < 0 ? o.ym : (dy > 0 ? o.yp : 0)) +
            (dz < 0 ? o.zm : (dz > 0 ? o.zp : 0));

@@ -76,6 +76,10 @@ cudaError_t flow_launch(int stencil, int storage, FlowOp op, const FlowLaunch& a
                         cudaStream_t s);
 cudaError_t thermal_launch(int storage, ThermOp op, const ThermLaunch& a, const Geom& g,
                            cudaStream_t s);
+// host run of the kernels' pull addressing over every node (stencil 0 D2Q9,
+// 1 D3Q19, 2 D3Q7): the number of wrong or out-of-range sources
+long long addressing_mismatches(int stencil, int nx, int ny, int nz);
+
 cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, double* out,
                             cudaStream_t s);
 // element conversion between float/double buffers (device to device)

@@ -197,6 +197,43 @@ cudaError_t thermal_launch(int storage, ThermOp op, const ThermLaunch& a, const 
     return cudaGetLastError();
 }
 
+namespace {
+// every (node, direction) pair: the source the kernels' offset arithmetic pulls
+// from, against x - s e_i wrapped periodically by plain modular arithmetic
+template <class L>
+long long check_addressing(int nx, int ny, int nz) {
+    long long bad = 0;
+    const long long N = (long long)nx * ny * nz;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                Cell c;
+                c.x = x;
+                c.y = y;
+                c.z = z;
+                c.n = x + (long long)nx * (y + (long long)ny * z);
+                c.active = true;
+                const Nbr o = neighbours(c, nx, ny, nz);
+                for (int i = 0; i < L::Q; ++i)
+                    for (int sgn = -1; sgn <= 1; sgn += 2) {
+                        const long long got = c.n + nbr_offset<L>(o, i, sgn);
+                        const int xs = ((x + sgn * L::cx(i)) % nx + nx) % nx;
+                        const int ys = ((y + sgn * L::cy(i)) % ny + ny) % ny;
+                        const int zs = ((z + sgn * L::cz(i)) % nz + nz) % nz;
+                        const long long want = xs + (long long)nx * (ys + (long long)ny * zs);
+                        bad += (got != want || got < 0 || got >= N);
+                    }
+            }
+    return bad;
+}
+}  // namespace
+
+long long addressing_mismatches(int stencil, int nx, int ny, int nz) {
+    if (stencil == 0) return check_addressing<D2Q9>(nx, ny, nz);
+    if (stencil == 2) return check_addressing<D3Q7>(nx, ny, nz);
+    return check_addressing<D3Q19>(nx, ny, nz);
+}
+
 cudaError_t finalize_launch(const double* partials, long long nblocks, int nv, double* out,
                             cudaStream_t s) {
     if (nv == 1)

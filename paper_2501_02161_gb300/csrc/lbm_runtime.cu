@@ -444,6 +444,15 @@ extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
 
+lbm_status lbm_check_addressing(int stencil, int nx, int ny, int nz, long long* mismatches) {
+    if (!mismatches) return fail(LBM_ERR_ARG, "mismatches is null");
+    if (stencil < 0 || stencil > 2) return fail(LBM_ERR_ARG, "unknown stencil");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(LBM_ERR_ARG, "lattice sizes must be positive");
+    if ((long long)nx * ny * nz > (1LL << 24)) return fail(LBM_ERR_ARG, "at most 2^24 nodes (a host loop)");
+    *mismatches = addressing_mismatches(stencil, nx, ny, nz);
+    return LBM_OK;
+}
+
 const char* lbm_version(void) { return "lbmadj 0.1 (sm_103a)"; }
 
 lbm_status lbm_create(lbm_ctx** out, int stencil, int nx, int ny, int nz, int storage, int thermal) {
