@@ -282,20 +282,25 @@ def random_fields(lat: Lattice, seed: int, scale: float = 1.0):
     return scale * rng.standard_normal(lat.n)
 
 
-def config_lattices(which: int, **kw):
-    """The synthetic stand-ins for the five benchmark configurations."""
-    if which == 1:
-        return pipe_bend_2d(**kw)
-    if which == 2:
-        return pipe_bend_3d(**kw)
-    if which == 3:
-        return heat_sink(**kw)
-    if which == 4:
-        kw.setdefault("nx", 96)
-        kw.setdefault("ny", 48)
-        kw.setdefault("nz", 24)
-        return heat_sink(**kw)
-    raise ValueError(which)
+# named stand-ins for the benchmark workloads (keyword overrides allowed)
+WORKLOADS = {
+    # 2D D2Q9 pipe bend 64 x 64, tau 0.6, gamma 0.5 (solved in FP64)
+    "pipe_bend_2d_64x64": lambda **kw: pipe_bend_2d(**kw),
+    # 3D D3Q19 pipe bend 64^3, filtered design field, Re 50 / 100 / 500
+    "pipe_bend_3d_64cubed": lambda **kw: pipe_bend_3d(**{"n": 64, "re": 50.0, **kw}),
+    # microchannel heat sink 128 x 64 x 32, D3Q19 + D3Q7, Pr 7
+    "heat_sink_128x64x32": lambda **kw: heat_sink(**{"nx": 128, "ny": 64, "nz": 32, "re": 50.0, **kw}),
+    # the differentiation workload: heat sink 96 x 48 x 24
+    "heat_sink_96x48x24": lambda **kw: heat_sink(**{"nx": 96, "ny": 48, "nz": 24, "re": 50.0, **kw}),
+}
+
+
+def workload(name: str, **kw) -> "Lattice":
+    """The lattice of a named workload (see WORKLOADS); served requests are
+    built by serve.lattice_for from their own shape and Re."""
+    if name not in WORKLOADS:
+        raise ValueError(f"unknown workload {name!r}; known: {sorted(WORKLOADS)}")
+    return WORKLOADS[name](**kw)
 
 
 def six_port_box(nx: int = 14, ny: int = 12, nz: int = 10, width: int = 3,

@@ -544,3 +544,4 @@ def test_sensitivity_vs_finite_difference_3d(oracle_mod):
 def test_sensitivity_vs_finite_difference_thermal(oracle_mod):
     lat = tiny_heat_sink()
     _fd_check(oracle_mod, lat, _sample_cells(lat, 5, 2))
+
