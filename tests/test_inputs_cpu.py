@@ -2,6 +2,7 @@
 path): named workload presets build the stated lattices."""
 import pytest
 
+
 def test_named_workloads_build_with_their_stated_shapes():
     """The named workload presets: shape, a valid flag field, gamma in [0, 1],
     an inlet and an outlet, and the temperature lattice where stated."""
