@@ -193,7 +193,8 @@ struct FlowArgs {
     R omega;                         // 1/tau
     R rho0;
     R src_in;                        // w_pin / (3 N_in): -dJ/df_i at VEL nodes
-    R ascale;                        // adjoint storage scale (16-bit adjoint), 1 otherwise
+    R ascale;                        // adjoint storage scale: 1 in every storage mode
+                                     // (the adjoint is stored at full precision)
     int model;                       // 0 EQ12, 1 LINEAR
 };
 
