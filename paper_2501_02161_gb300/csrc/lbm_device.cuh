@@ -505,8 +505,17 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
         Pop<T>::st(a.fout, (size_t)i * a.np + c.n, f[i], R(0));
 }
 
+// resident 256-thread blocks per SM asked of the compiler for the forward
+// step: with 16-bit populations 6 (40 registers, a few spilled bytes) beat 5
+// (48) by 4 % at 320^3, where the kernel is issue-bound; FP32 stays at the
+// compiler's 48 registers (6 blocks were 5 % slower at 64^3)
+template <class L, typename T>
+struct FwdMinBlocks {
+    static constexpr int value = (L::Q == 19 && sizeof(T) == 2) ? 6 : 1;
+};
+
 template <class L, typename T, typename TA, typename R, bool REDUCE>
-__global__ void __launch_bounds__(256) k_flow_step(FlowArgs<T, TA, R> a) {
+__global__ void __launch_bounds__(256, (FwdMinBlocks<L, T>::value)) k_flow_step(FlowArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
