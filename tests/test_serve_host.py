@@ -193,3 +193,32 @@ def test_host_budget_drops_the_oldest_offloaded_state(fakes):
     srv.close()
     assert held <= 1
     assert all(r.status == 0 for r in res)
+
+
+def test_request_contents_do_not_depend_on_the_arrival_rate():
+    """The offline and online streams differ only in arrival times, so their
+    results can be compared request by request."""
+    a = S.make_requests(64, seed=5, rate=None)
+    b = S.make_requests(64, seed=5, rate=3.0)
+    key = lambda r: (r.rid, r.shape, r.re, r.thermal, r.kind, r.design, r.seed)
+    assert [key(r) for r in a] == [key(r) for r in b]
+    assert all(r.arrival == 0.0 for r in a)
+    arr = [r.arrival for r in b]
+    assert arr == sorted(arr) and arr[-1] > 0
+    # an optimisation step refers to an earlier request's design, with its lattice
+    for r in a:
+        if r.kind == "opt":
+            base = a[r.design]
+            assert base.rid < r.rid and base.kind == "sens"
+            assert (base.shape, base.re, base.thermal, base.seed) == (r.shape, r.re, r.thermal, r.seed)
+
+
+def test_summary_counts_failures_and_takes_latency_percentiles():
+    res = []
+    for k in range(100):
+        r = S.Result(k, "sens", arrival=0.0, admitted=0.0, done=float(k + 1), status=0 if k % 10 else -4)
+        res.append(r)
+    s = S.summarize(res)
+    assert s["requests"] == 100 and s["completed"] == 90 and s["failed"] == 10
+    assert s["wall_s"] == 100.0 and s["sens_per_s"] == 0.9
+    assert s["p50_s"] == 50.5 and abs(s["p99_s"] - 99.01) < 1e-9
