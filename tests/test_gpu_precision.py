@@ -40,8 +40,9 @@ def test_sixteen_bit_error_vs_oracle(lat, storage):
     o = run_oracle(lat, 600, 400)
     errs = {k: float(rel(g[k], o[k])) for k in ("rho", "u", "sens", "fs") + (("T",) if "T" in o else ())}
     RESULTS[f"{lat.name}/{storage}"] = errs
-    if os.path.isdir("gpurun_out"):
-        json.dump(RESULTS, open("gpurun_out/precision_errors.json", "w"), indent=1)
+    out = os.environ.get("LBM_TEST_RECORDS")  # optional folder for the measured values
+    if out and os.path.isdir(out):
+        json.dump(RESULTS, open(os.path.join(out, "precision_errors.json"), "w"), indent=1)
     if storage in BOUND:
         for k, v in errs.items():
             assert np.isfinite(v) and v <= BOUND[storage][k], errs
