@@ -356,6 +356,16 @@ class Server:
                     break
             waiting = kept
             if not self.active:
+                if waiting:
+                    # nothing runs, so every idle design was evicted, and the
+                    # first waiting request still does not fit: it never will
+                    req = waiting.popleft()
+                    self.prep.drop(req)
+                    res = results[req.rid]
+                    res.status = C.LBM_ERR_OOM
+                    res.admitted = res.done = time.perf_counter() - t0
+                    done += 1
+                    continue
                 if order and realtime:
                     time.sleep(max(0.0, order[0].arrival - (time.perf_counter() - t0)))
                 continue

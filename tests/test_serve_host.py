@@ -222,3 +222,21 @@ def test_summary_counts_failures_and_takes_latency_percentiles():
     assert s["requests"] == 100 and s["completed"] == 90 and s["failed"] == 10
     assert s["wall_s"] == 100.0 and s["sens_per_s"] == 0.9
     assert s["p50_s"] == 50.5 and abs(s["p99_s"] - 99.01) < 1e-9
+
+
+def test_a_request_larger_than_the_budget_fails_instead_of_waiting_forever(fakes):
+    """With nothing running and every idle design evicted, a request that still
+    does not fit can never be admitted: it fails with LBM_ERR_OOM and the
+    others are served."""
+    from paper_2501_02161_gb300 import _capi as C
+    reqs = _reqs(20, seed=6)
+    sizes = sorted({S.footprint_of(r, "fp32") for r in reqs})
+    budget = sizes[-2]  # every shape but the largest fits
+    srv = S.Server("fp32", budget_bytes=budget, check_every=500, max_slots=4, device="cpu")
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    for q, r in zip(reqs, res):
+        too_big = S.footprint_of(q, "fp32") > budget
+        warm = q.kind == "opt" and r.warm
+        assert r.status == (C.LBM_ERR_OOM if too_big and not warm else 0), (q.rid, q.shape, r.status)
+    assert any(r.status == C.LBM_ERR_OOM for r in res) and any(r.status == 0 for r in res)
