@@ -75,3 +75,24 @@ def test_product_path_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "lbm_oracle" not in text, fn
+
+
+def test_no_gpu_means_a_loud_failure_not_a_cpu_path(libpath):
+    """On a machine without a usable GPU the library refuses to create a
+    context (LBM_ERR_CUDA with a message) and the Python face raises: there is
+    no CPU fallback for any step of the solve."""
+    import ctypes
+
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2501_02161_gb300 import _capi as C
+    L = C.lib()
+    ctx = ctypes.c_void_p()
+    assert L.lbm_create(ctypes.byref(ctx), C.LBM_D3Q19, 16, 16, 16, C.LBM_FP32, 0) == C.LBM_ERR_CUDA
+    assert not ctx.value and L.lbm_last_error()
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.solver import Solver
+    with pytest.raises(Exception):
+        Solver.from_lattice(I.pipe_bend_3d(n=16, width=4, re=20.0), storage="fp32")
