@@ -58,11 +58,14 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cap", type=int, default=CAP,
                    help="step cap per solve phase (lower it only for profiler launch lists)")
-    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve", "batchcmp"],
+    p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve", "batchcmp",
+                                                 "levelset"],
                    help="kernels: time the fused step kernels on a --roof-n lattice; "
                         "precision: heat sink in FP64/FP32/FP16/BF16 storage, error per field; "
-                        "autograd: the filtered / projected gradient loop")
-    p.add_argument("--iters", type=int, default=50, help="autograd mode: optimisation iterations")
+                        "autograd: the filtered / projected gradient loop; serve: the served "
+                        "streams; batchcmp: batched vs single-context throughput; levelset: the "
+                        "level-set optimiser on the 2D pipe bend")
+    p.add_argument("--iters", type=int, default=50, help="autograd / levelset modes: optimisation iterations")
     p.add_argument("--nreq", type=int, default=16, help="served requests per stream (serve mode: 256)")
     p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
@@ -139,6 +142,39 @@ def run_autograd(args):
                       "s_per_iter": round(dt / args.iters, 3),
                       "J": [round(h["J"], 6) for h in hist],
                       "loss": [round(h["loss"], 6) for h in hist]}))
+
+
+def run_levelset(args):
+    """The paper's optimiser on the 64 x 64 D2Q9 pipe bend (FP64, tau 0.6):
+    --iters level-set iterations (Eq. 14-15, lambda of Eq. 67, sigma 5e-3,
+    fluid fraction bound 0.08 pi as in the paper's 2D case), each a forward +
+    adjoint solve through the C-ABI, warm-started."""
+    import math
+
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.levelset import level_set_loop
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    lat = I.workload("pipe_bend_2d_64x64")
+    s = Solver.from_lattice(lat, storage="fp64", device="cuda:0")
+    t0 = time.perf_counter()
+    phi, hist = level_set_loop(s, lat, iters=args.iters, K=0.1, sigma=5e-3, vmax=0.08 * math.pi,
+                               tol=1e-6, max_steps=200000, check_every=1000)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    print(json.dumps({"mode": "levelset", "workload": "2D D2Q9 pipe bend 64x64, FP64, level set "
+                      "(K 0.1, sigma 5e-3, V_max 0.08 pi), forward + adjoint to 1e-6 warm-started",
+                      "iters": args.iters, "seconds": round(dt, 2),
+                      "s_per_iter": round(dt / max(args.iters, 1), 3),
+                      "J": [round(h["J"], 6) for h in hist],
+                      "fluid_fraction": [round(h["fluid_fraction"], 4) for h in hist],
+                      "lambda": [round(h["lambda"], 6) for h in hist]}))
 
 
 def run_serve(args, nreq=None, device="cuda:0"):
@@ -686,6 +722,8 @@ if __name__ == "__main__":
         run_precision(a)
     elif a.mode == "autograd":
         run_autograd(a)
+    elif a.mode == "levelset":
+        run_levelset(a)
     elif a.mode == "batchcmp":
         run_batchcmp(a)
     elif a.mode == "serve":
