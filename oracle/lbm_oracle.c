@@ -50,6 +50,10 @@ typedef struct {
     int thermal;
     double kappa_f, k_ratio, q_flux;
     double w_pin, w_tmean;
+    /* heat generation (Eq. 69, 71-72): source Q = beta_max (1 - gamma)(1 - T)
+     * added as w_k Q in the temperature collision; objective weight w_qgen
+     * of J_Q = -sum_nonwall Q.  Both 0 switch the variant off. */
+    double beta_max, w_qgen;
 } orc_problem;
 
 typedef struct {
@@ -578,11 +582,12 @@ static void thermal_collide_node(const lattice* LG, const orc_problem* P, uint8_
     double T = 0;
     for (int k = 0; k < LG->Q; k++) T += g[k];
     double tg = tau_g(P, gamma);
+    double Qsrc = P->beta_max * (1.0 - gamma) * (1.0 - T); /* Eq. 69 in Eq. 71 */
     for (int k = 0; k < LG->Q; k++) {
         double e[3];
         evec(LG, k, e);
         double geq = LG->w[k] * T * (1.0 + 4.0 * gamma * dot3(e, u));
-        out[k] = g[k] - (g[k] - geq) / tg;
+        out[k] = g[k] - (g[k] - geq) / tg + LG->w[k] * Qsrc;
     }
 }
 
@@ -688,14 +693,17 @@ static void thermal_collision_jacobians(const lattice* LF, const lattice* LG,
         evec(LG, k, e);
         double a = 1.0 + 4.0 * gamma * dot3(e, u);
         double geq = LG->w[k] * T * a;
+        /* the source w_k beta (1 - T) adds -w_k beta to every column */
         for (int l = 0; l < 7; l++)
-            Cg[k][l] = ((k == l) ? 1.0 : 0.0) - (((k == l) ? 1.0 : 0.0) - LG->w[k] * a) / tg;
+            Cg[k][l] = ((k == l) ? 1.0 : 0.0) - (((k == l) ? 1.0 : 0.0) - LG->w[k] * a) / tg
+                       - LG->w[k] * P->beta_max * (1.0 - gamma);
         for (int i = 0; i < LF->Q; i++) {
             double du[3];
             for (int b = 0; b < 3; b++) du[b] = LF->e[i][b] / P->rho0;
             Cf[k][i] = (ORC_MUTATION == 8 ? -1.0 : 1.0) * LG->w[k] * T * 4.0 * gamma * dot3(e, du) / tg;
         }
-        Cgam[k] = -(g[k] - geq) * dinv + LG->w[k] * T * 4.0 * dot3(e, u) / tg;
+        Cgam[k] = -(g[k] - geq) * dinv + LG->w[k] * T * 4.0 * dot3(e, u) / tg
+                  - LG->w[k] * P->beta_max * (1.0 - T);
     }
 }
 
@@ -860,10 +868,12 @@ void orc_thermal_adjoint_step(const orc_problem* P, const uint8_t* flags, const 
             gss[k] = gst[neighbour(P, n, LG.e[k][0], LG.e[k][1], LG.e[k][2]) * 7 + k];
         flow_u(&LF, P, f + n * Q, u);
         thermal_collision_jacobians(&LF, &LG, P, flags[n], gamma[n], u, g + n * 7, Cg, Cf, Cgam);
+        /* dJ_Q/dg_l = w_qgen beta_max (1 - gamma) at non-wall nodes (Eq. 72) */
+        double srcq = (ORC_MUTATION == 9 ? -1.0 : 1.0) * P->w_qgen * P->beta_max * (1.0 - gamma[n]);
         for (int l = 0; l < 7; l++) {
             double s = 0;
             for (int k = 0; k < 7; k++) s += Cg[k][l] * gss[k];
-            if (with_source && node_type(flags[n]) != T_WALL) s -= src;
+            if (with_source && node_type(flags[n]) != T_WALL) s -= src + srcq;
             gsc_new[n * 7 + l] = s;
         }
     }
@@ -929,9 +939,30 @@ void orc_thermal_coupling(const orc_problem* P, const uint8_t* flags, const doub
         double sg = 0;
         for (int k = 0; k < 7; k++) sg += gss[k] * Cgam[k];
         sensT[n] -= sg;
+        /* direct part of J_Q: dJ_Q/dgamma = w_qgen beta_max (1 - T) */
+        if (node_type(flags[n]) != T_WALL) {
+            double T = 0;
+            for (int k = 0; k < 7; k++) T += g[n * 7 + k];
+            sensT[n] += P->w_qgen * P->beta_max * (1.0 - T);
+        }
     }
     free(gs_all);
     free(gst);
+}
+
+/* J_Q = -sum over non-wall nodes of beta_max (1 - gamma)(1 - T), T of the
+ * post-B state g (Eq. 72), times w_qgen */
+double orc_objective_qgen(const orc_problem* P, const uint8_t* flags, const double* gamma,
+                          const double* g) {
+    long N = nnodes(P);
+    double s = 0;
+    for (long n = 0; n < N; n++) {
+        if (node_type(flags[n]) == T_WALL) continue;
+        double T = 0;
+        for (int k = 0; k < 7; k++) T += g[n * 7 + k];
+        s -= P->beta_max * (1.0 - gamma[n]) * (1.0 - T);
+    }
+    return P->w_qgen * s;
 }
 
 /* objective J = w_pin/(3 N_in) sum_inlet rho + w_tmean/N_nonwall sum_nonwall T

@@ -42,7 +42,8 @@ class Problem(ctypes.Structure):
                 ("gamma_model", ctypes.c_int), ("thermal", ctypes.c_int),
                 ("kappa_f", ctypes.c_double), ("k_ratio", ctypes.c_double),
                 ("q_flux", ctypes.c_double), ("w_pin", ctypes.c_double),
-                ("w_tmean", ctypes.c_double)]
+                ("w_tmean", ctypes.c_double), ("beta_max", ctypes.c_double),
+                ("w_qgen", ctypes.c_double)]
 
 
 _lib = None
@@ -103,6 +104,8 @@ def _load(path: str):
             fn.restype = None
         L.orc_objective.argtypes = [P, u8, d, d]
         L.orc_objective.restype = ctypes.c_double
+        L.orc_objective_qgen.argtypes = [P, u8, d, d]
+        L.orc_objective_qgen.restype = ctypes.c_double
         L.orc_lattice.restype = ctypes.c_int
         return L
 
@@ -123,10 +126,11 @@ def lattice_tables(which: int):
 
 
 def make_problem(stencil, nx, ny, nz, tau, rho0=1.0, gamma_model=0, thermal=False,
-                 kappa_f=0.0, k_ratio=1.0, q_flux=0.0, w_pin=1.0, w_tmean=0.0) -> Problem:
+                 kappa_f=0.0, k_ratio=1.0, q_flux=0.0, w_pin=1.0, w_tmean=0.0,
+                 beta_max=0.0, w_qgen=0.0) -> Problem:
     return Problem(int(stencil), int(nx), int(ny), int(nz), float(tau), float(rho0),
                    int(gamma_model), int(bool(thermal)), float(kappa_f), float(k_ratio),
-                   float(q_flux), float(w_pin), float(w_tmean))
+                   float(q_flux), float(w_pin), float(w_tmean), float(beta_max), float(w_qgen))
 
 
 def rel_change(a: float, b: float) -> float:
@@ -144,7 +148,7 @@ class Oracle:
         self.lat = lat
         self.P = make_problem(lat.stencil, lat.nx, lat.ny, lat.nz, lat.tau, lat.rho0,
                               lat.gamma_model, lat.thermal, lat.kappa_f, lat.k_ratio,
-                              lat.q_flux, lat.w_pin, lat.w_tmean)
+                              lat.q_flux, lat.w_pin, lat.w_tmean, lat.beta_max, lat.w_qgen)
         self.Q = 9 if lat.stencil == 0 else 19
         self.N = lat.n
         self.flags = np.ascontiguousarray(lat.flags, np.uint8)
@@ -213,8 +217,12 @@ class Oracle:
         return steps, res
 
     def objective(self) -> float:
-        return lib().orc_objective(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
-                                   _p(self.f), _p(self.g))
+        J = lib().orc_objective(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
+                                _p(self.f), _p(self.g))
+        if self.g is not None and self.P.w_qgen != 0.0:
+            J += lib().orc_objective_qgen(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
+                                          _p(self.gamma), _p(self.g))
+        return J
 
     # ---- thermal forward ------------------------------------------------
     def thermal_run(self, nsteps: int):

@@ -62,6 +62,8 @@ class Lattice:
     T0: float = 0.0            # initial temperature
     w_pin: float = 1.0         # objective weight of mean inlet pressure
     w_tmean: float = 0.0       # objective weight of mean temperature
+    beta_max: float = 0.0      # heat generation in the solid, Q = beta_max (1-gamma)(1-T) (Eq. 69)
+    w_qgen: float = 0.0        # objective weight of J_Q = -sum Q (Eq. 72)
     meta: dict = field(default_factory=dict)
 
     @property

@@ -61,6 +61,9 @@ class Solver:
 
     @classmethod
     def from_lattice(cls, lat, storage: str = "fp32", device=None) -> "Solver":
+        if getattr(lat, "beta_max", 0.0) != 0.0 or getattr(lat, "w_qgen", 0.0) != 0.0:
+            raise NotImplementedError("heat generation in the solid (beta_max, w_qgen; Eq. 69-72) "
+                                      "is not built in the CUDA solver")
         s = cls(lat.stencil, lat.nx, lat.ny, lat.nz, storage, lat.thermal, device)
         s.set_flags(torch.as_tensor(lat.flags, dtype=torch.uint8, device=s.device))
         s.set_gamma(torch.as_tensor(lat.gamma, dtype=s.rdtype, device=s.device))

@@ -9,6 +9,7 @@ import os
 
 import pytest
 
+import test_oracle_heatgen as H
 import test_oracle_pins as T
 from paper_2501_02161_gb300 import inputs as I
 
@@ -21,6 +22,7 @@ MUTATIONS = {
     6: "fixed-density outlet Jacobian with 3 w instead of 6 w",
     7: "adjoint objective source with the wrong sign",
     8: "thermal-to-flow coupling with the wrong sign",
+    9: "heat-generation objective source with the wrong sign",
 }
 
 
@@ -38,6 +40,7 @@ def pins(O):
     yield lambda: T.test_dot_product_adjoint_of_step(O, lat2)
     yield lambda: T.test_thermal_tangent_and_dot_product(O)
     yield lambda: T.test_sensitivity_vs_finite_difference_2d(O, I.GAMMA_EQ12)
+    yield lambda: H.test_sensitivity_with_heat_generation_vs_finite_difference(O)
 
 
 @pytest.mark.parametrize("k", sorted(MUTATIONS), ids=lambda k: MUTATIONS[k])
