@@ -549,6 +549,103 @@ void orc_flow_sensitivity(const orc_problem* P, const uint8_t* flags, const doub
 }
 
 /* ---------------------------------------------------------------------- */
+/* continuous adjoint LBM (Sec. 2.3), kept as the comparison the paper makes */
+/*   one iteration: adjoint collision C^T and reverse streaming (Eq. 30),     */
+/*   then the boundary conditions derived from the continuous Lagrangian:     */
+/*   fixed-density outlet whose unknowns are 4, 7, 8 (Eq. 27), velocity inlet */
+/*   whose reversed unknowns are 3, 6, 7 (Eq. 29), bounce-back walls.  The    */
+/*   objective enters through the inlet condition only; its 1/(3 W_in t_f)   */
+/*   is read as w_pin / (3 N_in) for the steady objective.  Written for D2Q9 */
+/*   with the inlet on a -x face and the outlet on a +y face, the geometry   */
+/*   these equations are printed for; returns -1 for anything else.          */
+/* ---------------------------------------------------------------------- */
+static int cont_geometry_ok(const orc_problem* P, const uint8_t* flags) {
+    if (P->stencil != 0) return 0;
+    long N = nnodes(P);
+    for (long n = 0; n < N; n++) {
+        int t = node_type(flags[n]), nv[3];
+        if (t != T_VEL && t != T_PRES) continue;
+        node_normal(flags[n], nv);
+        if (t == T_VEL && !(nv[0] == 1 && nv[1] == 0)) return 0;
+        if (t == T_PRES && !(nv[0] == 0 && nv[1] == -1)) return 0;
+    }
+    return 1;
+}
+
+int orc_cont_adjoint_step(const orc_problem* P, const uint8_t* flags, const double* gamma,
+                          const double* f, const double* fs, double* fs_new) {
+    if (!cont_geometry_ok(P, flags)) return -1;
+    lattice L;
+    flow_lattice(P, &L);
+    long N = nnodes(P);
+    const int Q = 9;
+    double* c = (double*)malloc(sizeof(double) * N * Q);
+    for (long n = 0; n < N; n++) {
+        if (node_type(flags[n]) == T_WALL) {
+            for (int i = 0; i < Q; i++) c[n * Q + i] = fs[n * Q + i];
+            continue;
+        }
+        double C[QMAX][QMAX];
+        collision_jacobian(&L, P, flags[n], gamma[n], f + n * Q, C);
+        for (int i = 0; i < Q; i++) {
+            double v = 0;
+            for (int m = 0; m < Q; m++) v += C[m][i] * fs[n * Q + m]; /* C^T */
+            c[n * Q + i] = v;
+        }
+    }
+    long nin = count_type(P, flags, T_VEL);
+    double s_in = (nin > 0) ? 2.0 * P->w_pin / (3.0 * (double)nin) : 0.0;
+    for (long n = 0; n < N; n++) {
+        double t[9];
+        for (int i = 0; i < Q; i++)
+            t[i] = c[neighbour(P, n, L.e[i][0], L.e[i][1], L.e[i][2]) * Q + i]; /* reverse stream */
+        int ty = node_type(flags[n]);
+        if (ty == T_WALL) {
+            for (int i = 1; i < Q; i++)
+                if (L.opp[i] > i) {
+                    double x = t[i];
+                    t[i] = t[L.opp[i]];
+                    t[L.opp[i]] = x;
+                }
+        } else if (ty == T_VEL) { /* Eq. 29 */
+            t[3] = t[1] - s_in;
+            t[6] = t[8] - s_in;
+            t[7] = t[5] - s_in;
+        } else if (ty == T_PRES) { /* Eq. 27 */
+            double K = 4.0 / 3.0 * t[2] + 1.0 / 3.0 * t[5] + 1.0 / 3.0 * t[6];
+            t[4] = t[2] - K;
+            t[7] = t[5] - K;
+            t[8] = t[6] - K;
+        }
+        for (int i = 0; i < Q; i++) fs_new[n * Q + i] = t[i];
+    }
+    free(c);
+    return 0;
+}
+
+/* J'(x) = -(1/tau) sum_i f*_i df^eq_i/dgamma (Eq. 32 without lambda) with the
+ * converged continuous adjoint f*; zero at wall nodes */
+void orc_cont_sensitivity(const orc_problem* P, const uint8_t* flags, const double* gamma,
+                          const double* f, const double* fs, double* sens) {
+    lattice L;
+    flow_lattice(P, &L);
+    long N = nnodes(P);
+    int Q = L.Q;
+    for (long n = 0; n < N; n++) {
+        if (node_type(flags[n]) == T_WALL) {
+            sens[n] = 0.0;
+            continue;
+        }
+        double rho, u[3], dg[QMAX];
+        moments(&L, f + n * Q, P->rho0, &rho, u);
+        equilibrium_dgamma(&L, u, gamma[n], P->gamma_model, P->rho0, dg);
+        double v = 0;
+        for (int i = 0; i < Q; i++) v += fs[n * Q + i] * dg[i];
+        sens[n] = -v / P->tau;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
 /* thermal lattice (D3Q7), u frozen from the converged flow                 */
 /*   g_C = g - (g - g^eq)/tau_g,  g^eq_k = w_k T (1 + 4 e_k.(gamma u))         */
 /*   tau_g = 1/2 + 4 kappa(gamma), kappa = kappa_f (gamma + (1-gamma) k_r)     */

@@ -107,6 +107,7 @@ def _load(path: str):
         L.orc_objective_qgen.argtypes = [P, u8, d, d]
         L.orc_objective_qgen.restype = ctypes.c_double
         L.orc_lattice.restype = ctypes.c_int
+        L.orc_cont_adjoint_step.restype = ctypes.c_int
         return L
 
 
@@ -372,6 +373,42 @@ class Oracle:
     def finish_thermal_adjoint(self):
         """Coupling term and thermal sensitivity from the converged g*_C."""
         self.coupling, self.sensT = self.thermal_coupling_of(self.gsc)
+
+    # ---- continuous adjoint (the comparison of Sec. 2.3) ----------------
+    def cont_adjoint_solve(self, tol: float, max_steps: int, check_every: int = 1000):
+        """Iterate the continuous adjoint (Eq. 27, 29, 30) from f* = 0 to the
+        residual rule on mean sum |f*|; the D2Q9 pipe-bend geometry only."""
+        fs = np.zeros(self.N * self.Q)
+        tmp = np.zeros_like(fs)
+        nw = self.nonwall
+
+        def quantity(x):
+            return float(np.abs(x.reshape(self.N, self.Q)[nw]).sum(axis=1).mean())
+        prev, steps, res = quantity(fs), 0, float("inf")
+        while steps < max_steps:
+            for _ in range(min(check_every, max_steps - steps)):
+                rc = lib().orc_cont_adjoint_step(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
+                                                 _p(self.gamma), _p(self.f), _p(fs), _p(tmp))
+                if rc != 0:
+                    raise ValueError("the continuous adjoint is written for D2Q9 with a -x inlet "
+                                     "and a +y outlet")
+                fs, tmp = tmp, fs
+                steps += 1
+            cur = quantity(fs)
+            if not np.isfinite(cur):
+                return steps, float("nan"), fs
+            res = rel_change(cur, prev)
+            prev = cur
+            if res < tol:
+                break
+        self.fs_cont = fs
+        return steps, res, fs
+
+    def cont_sensitivity(self) -> np.ndarray:
+        s = np.zeros(self.N)
+        lib().orc_cont_sensitivity(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
+                                   _p(self.gamma), _p(self.f), _p(self.fs_cont), _p(s))
+        return s
 
     # ---- whole pipeline -------------------------------------------------
     def solve_all(self, tol=1e-10, max_steps=200000, check_every=500, adj_tol=None):
