@@ -18,6 +18,8 @@
  *   thermal lattice   D3Q7 BGK with a gamma-interpolated relaxation time    [Eq. 71]
  *                     and its discrete adjoint, derived with the same recipe
  *                     (the paper's supplement that states them is absent).
+ *   comparison        the continuous adjoint LBM the paper argues against:
+ *                     C^T, reverse streaming, Eq. 27 / 29 boundaries     [Eq. 25-32]
  *
  * Layout: array of structures, f[n*Q + i], node n = x + nx*(y + ny*z).
  * Node flags follow the documented byte layout (type in bits 0-2, inward
@@ -551,25 +553,58 @@ void orc_flow_sensitivity(const orc_problem* P, const uint8_t* flags, const doub
 /* ---------------------------------------------------------------------- */
 /* continuous adjoint LBM (Sec. 2.3), kept as the comparison the paper makes */
 /*   one iteration: adjoint collision C^T and reverse streaming (Eq. 30),     */
-/*   then the boundary conditions derived from the continuous Lagrangian:     */
-/*   fixed-density outlet whose unknowns are 4, 7, 8 (Eq. 27), velocity inlet */
-/*   whose reversed unknowns are 3, 6, 7 (Eq. 29), bounce-back walls.  The    */
-/*   objective enters through the inlet condition only; its 1/(3 W_in t_f)   */
-/*   is read as w_pin / (3 N_in) for the steady objective.  Written for D2Q9 */
-/*   with the inlet on a -x face and the outlet on a +y face, the geometry   */
-/*   these equations are printed for; returns -1 for anything else.          */
+/*   then the boundary conditions derived from the continuous Lagrangian     */
+/*   (Eq. 25-29) and bounce-back walls.  At an open node with inward normal  */
+/*   n the reverse-streamed values f*_k with e_k.n < 0 came through the      */
+/*   periodic wrap (they point out of the domain) and are the unknowns:      */
+/*     fixed-density outlet (Eq. 27): f*_k = f*_opp(k) - K,                   */
+/*        K = 12 sum_{e_i.n > 0} w_i f*_i                                     */
+/*     velocity inlet (Eq. 29):       f*_k = f*_opp(k) - 2 w_pin / (3 N_in)   */
+/*   This is Eq. 27 for the bottom outlet (unknowns 4, 7, 8; K = 4/3 f*_2 +   */
+/*   1/3 f*_5 + 1/3 f*_6) and Eq. 29 for the left inlet (unknowns 3, 6, 7),   */
+/*   each derived from the vanishing boundary term of Eq. 25 with the Zou-He */
+/*   map of Eq. 7-8 substituted, which is why the same rule holds on every  */
+/*   face.  The rows of Eq. 26 and 28 for the tangential populations cannot  */
+/*   be satisfied (the inconsistency the paper points out) and are dropped,  */
+/*   as in the paper.  The objective's 1/(3 W_in t_f) is read as            */
+/*   w_pin / (3 N_in) for the steady objective.  D2Q9 only (the 3D forms are */
+/*   in the paper's unavailable Supplementary A); returns -1 otherwise.      */
 /* ---------------------------------------------------------------------- */
 static int cont_geometry_ok(const orc_problem* P, const uint8_t* flags) {
-    if (P->stencil != 0) return 0;
-    long N = nnodes(P);
-    for (long n = 0; n < N; n++) {
-        int t = node_type(flags[n]), nv[3];
-        if (t != T_VEL && t != T_PRES) continue;
-        node_normal(flags[n], nv);
-        if (t == T_VEL && !(nv[0] == 1 && nv[1] == 0)) return 0;
-        if (t == T_PRES && !(nv[0] == 0 && nv[1] == -1)) return 0;
+    (void)flags;
+    return P->stencil == 0;
+}
+
+/* the continuous adjoint boundary condition at one node, in place on its
+ * reverse-streamed values t (s_in = 2 w_pin / (3 N_in)) */
+static void cont_bc_node(const lattice* L, uint8_t fl, double s_in, double* t) {
+    int ty = node_type(fl);
+    if (ty == T_FLUID) return;
+    if (ty == T_WALL) {
+        for (int i = 1; i < L->Q; i++)
+            if (L->opp[i] > i) {
+                double x = t[i];
+                t[i] = t[L->opp[i]];
+                t[L->opp[i]] = x;
+            }
+        return;
     }
-    return 1;
+    int n[3];
+    node_normal(fl, n);
+    if (ORC_MUTATION == 10) { /* the printed bottom-outlet / left-inlet indices on every face */
+        n[0] = ty == T_VEL ? 1 : 0;
+        n[1] = ty == T_VEL ? 0 : 1;
+        n[2] = 0;
+    }
+    double K = 0;
+    if (ty == T_PRES)
+        for (int i = 0; i < L->Q; i++)
+            if (L->e[i][0] * n[0] + L->e[i][1] * n[1] + L->e[i][2] * n[2] > 0) K += 12.0 * L->w[i] * t[i];
+    double sub = ty == T_PRES ? K : s_in;
+    double old[QMAX];
+    for (int i = 0; i < L->Q; i++) old[i] = t[i];
+    for (int k = 0; k < L->Q; k++)
+        if (L->e[k][0] * n[0] + L->e[k][1] * n[1] + L->e[k][2] * n[2] < 0) t[k] = old[L->opp[k]] - sub;
 }
 
 int orc_cont_adjoint_step(const orc_problem* P, const uint8_t* flags, const double* gamma,
@@ -599,27 +634,22 @@ int orc_cont_adjoint_step(const orc_problem* P, const uint8_t* flags, const doub
         double t[9];
         for (int i = 0; i < Q; i++)
             t[i] = c[neighbour(P, n, L.e[i][0], L.e[i][1], L.e[i][2]) * Q + i]; /* reverse stream */
-        int ty = node_type(flags[n]);
-        if (ty == T_WALL) {
-            for (int i = 1; i < Q; i++)
-                if (L.opp[i] > i) {
-                    double x = t[i];
-                    t[i] = t[L.opp[i]];
-                    t[L.opp[i]] = x;
-                }
-        } else if (ty == T_VEL) { /* Eq. 29 */
-            t[3] = t[1] - s_in;
-            t[6] = t[8] - s_in;
-            t[7] = t[5] - s_in;
-        } else if (ty == T_PRES) { /* Eq. 27 */
-            double K = 4.0 / 3.0 * t[2] + 1.0 / 3.0 * t[5] + 1.0 / 3.0 * t[6];
-            t[4] = t[2] - K;
-            t[7] = t[5] - K;
-            t[8] = t[6] - K;
-        }
+        cont_bc_node(&L, flags[n], s_in, t);
         for (int i = 0; i < Q; i++) fs_new[n * Q + i] = t[i];
     }
     free(c);
+    return 0;
+}
+
+/* the continuous adjoint boundary condition of one node applied to given
+ * reverse-streamed values (for the pins); D2Q9 only, returns -1 otherwise */
+int orc_cont_node_bc(const orc_problem* P, uint8_t fl, double s_in, const double* t_in,
+                     double* t_out) {
+    if (P->stencil != 0) return -1;
+    lattice L;
+    flow_lattice(P, &L);
+    for (int i = 0; i < L.Q; i++) t_out[i] = t_in[i];
+    cont_bc_node(&L, fl, s_in, t_out);
     return 0;
 }
 

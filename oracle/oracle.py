@@ -108,6 +108,8 @@ def _load(path: str):
         L.orc_objective_qgen.restype = ctypes.c_double
         L.orc_lattice.restype = ctypes.c_int
         L.orc_cont_adjoint_step.restype = ctypes.c_int
+        L.orc_cont_node_bc.argtypes = [P, ctypes.c_uint8, ctypes.c_double, d, d]
+        L.orc_cont_node_bc.restype = ctypes.c_int
         return L
 
 
@@ -377,7 +379,7 @@ class Oracle:
     # ---- continuous adjoint (the comparison of Sec. 2.3) ----------------
     def cont_adjoint_solve(self, tol: float, max_steps: int, check_every: int = 1000):
         """Iterate the continuous adjoint (Eq. 27, 29, 30) from f* = 0 to the
-        residual rule on mean sum |f*|; the D2Q9 pipe-bend geometry only."""
+        residual rule on mean sum |f*|; D2Q9 lattices only."""
         fs = np.zeros(self.N * self.Q)
         tmp = np.zeros_like(fs)
         nw = self.nonwall
@@ -390,8 +392,8 @@ class Oracle:
                 rc = lib().orc_cont_adjoint_step(ctypes.byref(self.P), _p(self.flags, ctypes.c_uint8),
                                                  _p(self.gamma), _p(self.f), _p(fs), _p(tmp))
                 if rc != 0:
-                    raise ValueError("the continuous adjoint is written for D2Q9 with a -x inlet "
-                                     "and a +y outlet")
+                    raise ValueError("the continuous adjoint is written for D2Q9 only (the 3D "
+                                     "boundary forms are not printed in the paper)")
                 fs, tmp = tmp, fs
                 steps += 1
             cur = quantity(fs)

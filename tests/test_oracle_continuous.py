@@ -2,8 +2,11 @@
 the paper draws: its interior iteration is the discrete one, its boundary
 conditions (Eq. 27, 29) are those derived from the continuous Lagrangian.
 The interior operator is pinned by commutation with the discrete iteration;
-on the 2D pipe bend the discrete sensitivity matches central finite
-differences while the continuous one does not, which is the paper's point."""
+the boundary rows by the vanishing boundary term of Eq. 25 (Eq. 28 at
+inlets) under the Zou-He variations of Eq. 7-8 on every face, by the printed
+bottom-outlet / left-inlet forms and by mirror symmetry.  On the 2D pipe bend
+the discrete sensitivity matches central finite differences while the
+continuous one does not, which is the paper's point."""
 import ctypes
 
 import numpy as np
@@ -78,4 +81,142 @@ def test_discrete_sensitivity_is_exact_and_continuous_is_not(oracle_mod):
     err_disc = np.linalg.norm(disc[cells] - fd) / np.linalg.norm(fd)
     err_cont = np.linalg.norm(cont[cells] - fd) / np.linalg.norm(fd)
     assert err_disc < 1e-6
-    assert err_cont > 0.1  # measured 0.9: sign errors at inlet nodes, ~0.3x elsewhere
+    # measured 1.14 on this 10 x 10 case (and 1.15 / 1.09 at Re 0.15 / 1.5 on the
+    # same lattice: no growth with Re at this size, unlike the paper's Fig. 7
+    # on its optimisation lattices)
+    assert err_cont > 0.1
+
+
+# ---------------------------------------------------------------------------
+# the boundary conditions of the continuous adjoint (Eq. 25-29)
+# ---------------------------------------------------------------------------
+D2Q9_MIRROR_Y = [0, 1, 4, 3, 2, 8, 7, 6, 5]
+
+
+def _node_bc(O, P, fl, s_in, t):
+    out = np.zeros(9)
+    assert O.lib().orc_cont_node_bc(ctypes.byref(P), ctypes.c_uint8(fl), ctypes.c_double(s_in),
+                                    O._p(np.ascontiguousarray(t, float)), O._p(out)) == 0
+    return out
+
+
+def _bc_jacobian(O, P, fl):
+    B = np.zeros(81)
+    O.lib().orc_node_bc_jacobian(ctypes.byref(P), ctypes.c_uint8(fl), O._p(B))
+    return B.reshape(9, 9)   # B[i, j] = d f_i / d f_S,j
+
+
+def test_outlet_and_inlet_rules_are_eq27_and_eq29_as_printed(oracle_mod):
+    """Bottom outlet (inward normal +y) and left inlet (+x): the printed forms."""
+    O = oracle_mod
+    P = O.make_problem(0, 4, 4, 1, 0.8)
+    rng = np.random.default_rng(7)
+    t = rng.standard_normal(9)
+    out = _node_bc(O, P, I.make_flag(I.PRES, (0, 1, 0)), 0.0, t)
+    K = 4 / 3 * t[2] + 1 / 3 * t[5] + 1 / 3 * t[6]
+    want = t.copy()
+    want[4], want[7], want[8] = t[2] - K, t[5] - K, t[6] - K
+    assert np.allclose(out, want, rtol=0, atol=1e-15)
+    s = 0.37
+    out = _node_bc(O, P, I.make_flag(I.VEL, (1, 0, 0)), s, t)
+    want = t.copy()
+    want[3], want[6], want[7] = t[1] - s, t[8] - s, t[5] - s
+    assert np.allclose(out, want, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("normal", [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)])
+@pytest.mark.parametrize("kind", [I.VEL, I.PRES])
+def test_boundary_term_of_eq25_vanishes_on_every_face(oracle_mod, normal, kind):
+    """The continuous adjoint boundary rows come from requiring the boundary
+    term of Eq. 21 (Eq. 25 at outlets; with the objective's dJ at inlets,
+    Eq. 28) to vanish for the variations the Zou-He map (Eq. 7-8) allows.
+    For any adjoint values at the node, after the update the term
+    sum_i (e_i.n_out) f*_i df_i (+ dJ at inlets), with df = B' df_S, must
+    vanish for every df_S on the outgoing populations (the rows that define
+    the unknowns), while for df_S on the tangential populations it does not
+    (the rows the paper shows cannot be satisfied).  The values with a source
+    inside the domain must pass through unchanged."""
+    O = oracle_mod
+    P = O.make_problem(0, 4, 4, 1, 0.8)
+    e, w, opp = O.lattice_tables(0)
+    n_in = np.array(normal, float)
+    n_out = -n_in
+    fl = I.make_flag(kind, normal)
+    sp = 0.21 if kind == I.VEL else 0.0   # dJ per population of an inlet node: w_pin/(3 N_in)
+    B = _bc_jacobian(O, P, fl)
+    rng = np.random.default_rng(11)
+    en = e @ n_in
+    outgoing = np.where(en < 0)[0]
+    tangential = np.where(en == 0)[0]
+    for trial in range(5):
+        t = rng.standard_normal(9)
+        fstar = _node_bc(O, P, fl, 2 * sp, t)
+        # the reverse-streamed values with e.n_in >= 0 came from inside the
+        # domain (x + e_i is a lattice node): they are kept; the outgoing ones
+        # came through the periodic wrap, and the result must not depend on them
+        keep = en >= 0
+        assert np.array_equal(fstar[keep], t[keep])
+        t2 = t.copy()
+        t2[~keep] = rng.standard_normal(int((~keep).sum()))
+        assert np.allclose(_node_bc(O, P, fl, 2 * sp, t2), fstar, rtol=0, atol=1e-15)
+        for j in outgoing:
+            dfs = np.zeros(9)
+            dfs[j] = 1.0
+            df = B @ dfs
+            term = float(np.sum((e @ n_out) * fstar * df) + sp * df.sum())
+            assert abs(term) < 1e-13, (trial, j, term)
+        bad = 0.0
+        for j in tangential:
+            dfs = np.zeros(9)
+            dfs[j] = 1.0
+            df = B @ dfs
+            bad = max(bad, abs(float(np.sum((e @ n_out) * fstar * df) + sp * df.sum())))
+        assert bad > 1e-3
+
+
+def _mirror_y_lattice(lat):
+    """The same 2D problem reflected in y (outlet moved from the top face to
+    the bottom face)."""
+    ny, nx = lat.ny, lat.nx
+    fl = lat.flags.reshape(ny, nx)[::-1].copy()
+    kind = fl & 7
+    code = (fl >> 3) & 7
+    open_ = (kind == I.VEL) | (kind == I.PRES)
+    swap = {2: 3, 3: 2}
+    code2 = np.vectorize(lambda c: swap.get(int(c), int(c)))(code)
+    fl = np.where(open_, (fl & 0xC7) | (code2.astype(np.uint8) << 3), fl).astype(np.uint8)
+    bc = lat.bcval.reshape(ny, nx, 4)[::-1].copy()
+    bc[..., 1] *= -1.0
+    gam = lat.gamma.reshape(ny, nx)[::-1].copy()
+    return I.Lattice(lat.name + "_mirrored", lat.stencil, nx, ny, 1, fl.ravel(), gam.ravel(),
+                     bc.ravel(), tau=lat.tau, gamma_model=lat.gamma_model)
+
+
+def _mirror_y_field(a, nx, ny, Q=9):
+    a = np.asarray(a).reshape(ny, nx, Q)[::-1]
+    return a[..., D2Q9_MIRROR_Y] if Q == 9 else a
+
+
+def test_continuous_adjoint_is_mirror_symmetric(oracle_mod):
+    """A pipe bend with its outlet on the top face and its mirror image with
+    the outlet on the bottom face (the face Eq. 27 is printed for) give
+    mirrored continuous adjoints and sensitivities."""
+    O = oracle_mod
+    lat = I.pipe_bend_2d(nx=10, ny=10, width=3, tau=0.9, gamma_value=0.7)
+    rng = np.random.default_rng(1)
+    lat.gamma = np.where((lat.flags & 7) == I.WALL, 0.0, 0.4 + 0.5 * rng.random(lat.n))
+    lm = _mirror_y_lattice(lat)
+    res = []
+    for L in (lat, lm):
+        orc = O.Oracle(L)
+        orc.flow_solve(1e-14, 400000, 1000)
+        steps, r, fs = orc.cont_adjoint_solve(1e-14, 400000, 1000)
+        assert r < 1e-12
+        res.append((orc.f.copy(), fs.copy(), orc.cont_sensitivity()))
+    (f0, fs0, s0), (f1, fs1, s1) = res
+    nx, ny = lat.nx, lat.ny
+    assert np.allclose(_mirror_y_field(f0, nx, ny), f1.reshape(ny, nx, 9), rtol=0, atol=1e-12)
+    assert np.allclose(_mirror_y_field(fs0, nx, ny), fs1.reshape(ny, nx, 9), rtol=0,
+                       atol=1e-10 * np.abs(fs0).max())
+    assert np.allclose(s0.reshape(ny, nx)[::-1], s1.reshape(ny, nx), rtol=0,
+                       atol=1e-10 * np.abs(s0).max())
