@@ -95,12 +95,42 @@ typedef struct {
     double k_ratio;    /* solid/fluid conductivity ratio: kappa = kappa_f (gamma + (1-gamma) k_ratio) */
     double q_flux;     /* heat per step added at HEAT wall nodes */
     double T0;         /* initial temperature (and 16-bit storage offset) */
+    double beta_max;   /* heat generation in the solid, Q = beta_max (1 - gamma)(1 - T), added as
+                          w_k Q in the temperature collision (Eq. 69, 71); 0 switches it off */
 } lbm_params;
 
 typedef struct {
     double w_pin;      /* weight of J_p = (1/(3 N_in)) sum_{VEL nodes} rho  (Eq. 34, steady) */
     double w_tmean;    /* weight of J_T = (1/N_nonwall) sum_{non-wall nodes} T */
+    double w_qgen;     /* weight of J_Q = -sum_{non-wall nodes} Q (Eq. 72), Q of Eq. 69 */
 } lbm_objective;
+
+/* The problem in the paper's physical terms (Sec. 2.1, Eq. 3; Sec. 3.3):
+ *   nu = U L / Re,  tau = 1/2 + 3 nu                      (Eq. 3, c_s^2 = 1/3)
+ *   U  = u_ref, or sqrt(dp / rho0) when u_ref <= 0 and dp > 0: the velocity
+ *        estimated from a pressure drop dp = p_in - p_out (Eq. 70, the
+ *        pressure-driven heat sink)
+ *   kappa_f = nu / Pr                                     (Pr = nu / kappa_f)
+ * lbm_physics_to_params does the conversion (host only, no device needed);
+ * lbm_set_physics converts and then behaves as lbm_set_params. */
+typedef struct {
+    double re;         /* Reynolds number, > 0 */
+    double u_ref;      /* velocity scale U (lattice units), e.g. the inlet's peak speed */
+    double l_ref;      /* length scale L (nodes), e.g. the inlet width; > 0 */
+    double dp;         /* pressure drop defining U when u_ref <= 0 (Eq. 70) */
+    double pr;         /* Prandtl number (> 0 with the thermal lattice; unused without) */
+    double rho0;       /* as in lbm_params */
+    int gamma_model;
+    double k_ratio;
+    double q_flux;
+    double T0;
+    double beta_max;
+} lbm_physics;
+
+/* tau and kappa_f from Re, U, L and Pr; the other fields are copied.
+ * Errors: LBM_ERR_ARG (null, re <= 0, l_ref <= 0, no velocity scale,
+ * rho0 <= 0, pr < 0, non-finite values). */
+lbm_status lbm_physics_to_params(const lbm_physics* ph, lbm_params* out);
 
 typedef struct {
     double tol;          /* stop when |I(t)-I(t-K)|/|I(t)| < tol; tol <= 0: run exactly max_steps */
@@ -147,9 +177,30 @@ lbm_status lbm_set_gamma(lbm_ctx* ctx, const void* gamma, size_t n, int dtype, i
 lbm_status lbm_set_bc_values(lbm_ctx* ctx, const void* values, size_t n, int dtype,
                              int on_device);
 /* Physical parameters.  tau <= 0.5, rho0 <= 0, kappa_f < 0 with thermal on,
- * k_ratio <= 0 or an unknown gamma model give LBM_ERR_ARG. */
+ * k_ratio <= 0, beta_max < 0 (or != 0 without the thermal lattice) or an
+ * unknown gamma model give LBM_ERR_ARG. */
 lbm_status lbm_set_params(lbm_ctx* ctx, const lbm_params* p);
+/* Parameters from Re, U, L and Pr (see lbm_physics); same errors as
+ * lbm_physics_to_params and lbm_set_params (pr <= 0 with thermal on is
+ * LBM_ERR_ARG). */
+lbm_status lbm_set_physics(lbm_ctx* ctx, const lbm_physics* ph);
+/* Objective weights.  Non-finite weights, or w_qgen != 0 without the
+ * thermal lattice, give LBM_ERR_ARG. */
 lbm_status lbm_set_objective(lbm_ctx* ctx, const lbm_objective* obj);
+
+/* Boundary values of one face of the lattice box (the per-node form is
+ * lbm_set_bc_values).  face: the inward normal code of the face (0: x = 0,
+ * 1: x = nx-1, 2: y = 0, 3: y = ny-1, 4: z = 0, 5: z = nz-1).  kind:
+ * LBM_VEL (Zou-He velocity inlet, Eq. 7) or LBM_PRES (fixed-density outlet,
+ * Eq. 8).  Only the nodes of that face whose flag is that kind with that
+ * normal are written: values holds 4 numbers per such node, in increasing
+ * node order ((ux, uy, uz, T_in) or (rho_out, 0, 0, 0)), or just 4 numbers
+ * applied to all of them (n = 4).  Other nodes keep their values.  Needs
+ * lbm_set_flags (LBM_ERR_ORDER).  Errors: LBM_ERR_ARG (bad face, kind or
+ * dtype, no such node on the face, n neither 4 nor 4 x their count). */
+enum { LBM_VEL = 2, LBM_PRES = 3 };
+lbm_status lbm_set_bc(lbm_ctx* ctx, int face, int kind, const void* values, size_t n, int dtype,
+                      int on_device);
 
 /* Forward solve (Eq. 35): the flow to its residual tolerance, then, with the
  * thermal lattice on, the temperature with the converged velocity frozen.
@@ -162,6 +213,31 @@ lbm_status lbm_forward(lbm_ctx* ctx, const lbm_solve_opts* opts, lbm_report* rep
  * temperature adjoint first (thermal on), then the flow adjoint with the
  * thermal coupling term.  Needs a completed lbm_forward (else LBM_ERR_ORDER). */
 lbm_status lbm_adjoint(lbm_ctx* ctx, const lbm_solve_opts* opts, lbm_report* rep);
+
+/* The solve sequence phase by phase.  lbm_forward runs LBM_PHASE_FLOW then
+ * (thermal on) LBM_PHASE_TEMPERATURE; lbm_adjoint runs (thermal on)
+ * LBM_PHASE_TEMPERATURE_ADJOINT, the thermal-to-flow coupling, then
+ * LBM_PHASE_FLOW_ADJOINT.  lbm_solve_phase runs one of them with its own
+ * tolerance and step cap, so a caller can stop each phase where it wants (for
+ * example: replay another solver's step counts phase by phase).  Order: the
+ * temperature phase needs a completed flow phase (Eq. 71 runs on the frozen
+ * converged flow); the temperature adjoint needs a completed forward; the
+ * flow adjoint needs a completed forward and, thermal on, a completed
+ * temperature adjoint (the coupling term of its source) -- else
+ * LBM_ERR_ORDER.  opts->reset restarts the phase's populations; restarting the
+ * flow phase also restarts the temperature populations, restarting the
+ * temperature adjoint also restarts the flow adjoint.  A completed phase
+ * invalidates the results of the phases after it.  rep (may be null) gets
+ * this phase's steps, residual and I; rep->J is the objective so far.
+ * Errors: LBM_ERR_ARG (unknown phase, temperature phase without the thermal
+ * lattice), LBM_ERR_ORDER, LBM_ERR_DIVERGED; LBM_NOT_CONVERGED as lbm_forward. */
+typedef enum {
+    LBM_PHASE_FLOW = 0,
+    LBM_PHASE_TEMPERATURE = 1,
+    LBM_PHASE_FLOW_ADJOINT = 2,
+    LBM_PHASE_TEMPERATURE_ADJOINT = 3
+} lbm_phase;
+lbm_status lbm_solve_phase(lbm_ctx* ctx, int phase, const lbm_solve_opts* opts, lbm_report* rep);
 
 /* dJ/dgamma per node (Eq. 66 without the volume multiplier lambda, plus the
  * temperature terms when thermal is on), n = nx*ny*nz values of dtype into
@@ -248,9 +324,22 @@ size_t lbm_footprint_bytes(int stencil, int nx, int ny, int nz, int storage, int
 
 /* storage: the storage every admitted context must use; check_every: K, even,
  * the residual-check interval (and graph length); max_slots: resident contexts
- * at most.  Errors: LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (FP64), LBM_ERR_OOM. */
-lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots);
+ * at most; hbm_budget_bytes: device memory the batch's contexts may hold
+ * together (0: no limit).  A context counts against the budget, with its
+ * lbm_footprint_bytes, from its first admission until lbm_batch_release or
+ * lbm_destroy, so finished contexts kept for a warm start keep counting.
+ * Errors: LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (FP64), LBM_ERR_OOM. */
+lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots,
+                            size_t hbm_budget_bytes);
 void lbm_batch_destroy(lbm_batch* b);
+
+/* Stop counting a context against the batch's budget (it must not be
+ * running in the batch: LBM_ERR_ORDER; unknown contexts: LBM_ERR_ARG).
+ * lbm_destroy of a counted context releases it. */
+lbm_status lbm_batch_release(lbm_batch* b, lbm_ctx* ctx);
+
+/* The budget and the bytes counted against it now. */
+lbm_status lbm_batch_memory(lbm_batch* b, size_t* budget, size_t* held);
 
 /* Queue a context (inputs set, D3Q19, the batch's storage) for a forward +
  * adjoint solve with opts->tol and opts->max_steps per phase (opts->check_every
@@ -258,7 +347,8 @@ void lbm_batch_destroy(lbm_batch* b);
  * context's previous populations).  The context must not be used by other
  * calls until it is returned by lbm_batch_poll.  *slot receives its slot id.
  * Errors: LBM_ERR_ARG (wrong storage/stencil, batch full), LBM_ERR_ORDER
- * (inputs missing). */
+ * (inputs missing), LBM_ERR_OOM (a context not yet counted does not fit the
+ * budget now: nothing changes; admit it after releasing others). */
 lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* ctx, const lbm_solve_opts* opts, int* slot);
 
 /* Advance every admitted context by K steps of its current phase and move
@@ -301,8 +391,12 @@ lbm_status lbm_batch_poll(lbm_batch* b, int* slots, lbm_ctx** ctxs, lbm_report* 
  * The lattice may need at most 32768 reduction blocks (about 8.3 million
  * nodes of 256-node tiles); larger lattices give LBM_ERR_ARG.  The first call
  * on a device looks up the scratch array's device address, so make that first
- * call before any stream capture.  Every call shares the one scratch array, so
- * calls that overlap on the GPU (different streams, no ordering) race.
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or any teardown of the device's primary
+ * context) the library's device code is loaded again and the kept address is
+ * stale, so this entry point must not be used on that device again in the
+ * same process.  Every call shares the one scratch array, so calls that
+ * overlap on the GPU (different streams, no ordering) race.
  * --------------------------------------------------------------------------- */
 typedef struct {
     int stencil;         /* lbm_stencil */

@@ -22,17 +22,28 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_OFS, LBM_BF16_OFS = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_GAMMA_EQ12, LBM_GAMMA_LINEAR = 0, 1
+LBM_VEL, LBM_PRES = 2, 3
+LBM_PHASE_FLOW, LBM_PHASE_TEMPERATURE, LBM_PHASE_FLOW_ADJOINT, LBM_PHASE_TEMPERATURE_ADJOINT = 0, 1, 2, 3
 
 
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("gamma_model", ctypes.c_int), ("kappa_f", ctypes.c_double),
                 ("k_ratio", ctypes.c_double), ("q_flux", ctypes.c_double),
-                ("T0", ctypes.c_double)]
+                ("T0", ctypes.c_double), ("beta_max", ctypes.c_double)]
 
 
 class lbm_objective(ctypes.Structure):
-    _fields_ = [("w_pin", ctypes.c_double), ("w_tmean", ctypes.c_double)]
+    _fields_ = [("w_pin", ctypes.c_double), ("w_tmean", ctypes.c_double),
+                ("w_qgen", ctypes.c_double)]
+
+
+class lbm_physics(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("u_ref", ctypes.c_double), ("l_ref", ctypes.c_double),
+                ("dp", ctypes.c_double), ("pr", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("gamma_model", ctypes.c_int), ("k_ratio", ctypes.c_double),
+                ("q_flux", ctypes.c_double), ("T0", ctypes.c_double),
+                ("beta_max", ctypes.c_double)]
 
 
 class lbm_solve_opts(ctypes.Structure):
@@ -67,8 +78,12 @@ SIGNATURES = {
     "lbm_set_bc_values": (_I, [_VP, _VP, _SZ, _I, _I]),
     "lbm_set_params": (_I, [_VP, ctypes.POINTER(lbm_params)]),
     "lbm_set_objective": (_I, [_VP, ctypes.POINTER(lbm_objective)]),
+    "lbm_physics_to_params": (_I, [ctypes.POINTER(lbm_physics), ctypes.POINTER(lbm_params)]),
+    "lbm_set_physics": (_I, [_VP, ctypes.POINTER(lbm_physics)]),
+    "lbm_set_bc": (_I, [_VP, _I, _I, _VP, _SZ, _I, _I]),
     "lbm_forward": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_adjoint": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
+    "lbm_solve_phase": (_I, [_VP, _I, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_sensitivity": (_I, [_VP, _VP, _I, _I]),
     "lbm_get_fields": (_I, [_VP, _VP, _VP, _VP, _I, _I]),
     "lbm_get_objective": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
@@ -76,7 +91,9 @@ SIGNATURES = {
     "lbm_time_steps": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "lbm_flow_step_noalloc": (_I, [ctypes.POINTER(lbm_step_desc), _VP]),
     "lbm_footprint_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I, _I]),
-    "lbm_batch_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _SZ]),
+    "lbm_batch_release": (_I, [_VP, _VP]),
+    "lbm_batch_memory": (_I, [_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "lbm_batch_destroy": (None, [_VP]),
     "lbm_batch_admit": (_I, [_VP, _VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(_I)]),
     "lbm_state_bytes": (ctypes.c_size_t, [_VP]),

@@ -86,16 +86,20 @@ struct lbm_ctx {
     double* hres = nullptr;  // pinned, 4 doubles
 
     Geom geom{};
-    lbm_params prm{0.6, 1.0, 0, 0.0, 1.0, 0.0, 0.0};
-    lbm_objective obj{1.0, 0.0};
+    lbm_params prm{0.6, 1.0, 0, 0.0, 1.0, 0.0, 0.0, 0.0};
+    lbm_objective obj{1.0, 0.0, 0.0};
     long long n_in = 0, n_nw = 0;
     bool have_flags = false, have_gamma = false, have_bc = false, have_params = false;
     bool fwd_done = false, adj_done = false;
+    bool flow_done = false, tadj_done = false;  // phase-level completion (lbm_solve_phase)
     bool fstate = false, astate = false;  // populations hold a usable (warm-start) state
-    double J_p = 0.0, J_T = 0.0;
+    double J_p = 0.0, J_T = 0.0, J_Q = 0.0;
+    double J() const { return J_p + (thermal ? J_T + J_Q : 0.0); }
     double last_I[4] = {0, 0, 0, 0};
 
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+    std::vector<uint8_t> hflags;   // host copy of the flags (per-face boundary values)
+    lbm_batch* holder = nullptr;   // batch whose memory budget counts this context
 
     void drop_graphs() {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -104,6 +108,8 @@ struct lbm_ctx {
 };
 
 namespace {
+// a destroyed context stops counting against its batch's memory budget
+void batch_forget(lbm_batch* b, lbm_ctx* c);
 
 void* dalloc(size_t bytes, cudaError_t* err) {
     void* p = nullptr;
@@ -181,10 +187,14 @@ ThermLaunch therm_base(lbm_ctx* c) {
     a.T0 = c->prm.T0;
     a.src_T = c->n_nw > 0 ? c->obj.w_tmean / (double)c->n_nw : 0.0;
     a.ascale = 1.0;
+    a.beta = c->prm.beta_max;
+    a.src_q = c->obj.w_qgen * c->prm.beta_max;
     return a;
 }
 
-int phase_nv(int ph) { return ph == PH_FLOW ? 2 : 1; }
+// values a phase's reducing step sums: flow |u| and inlet rho; temperature T
+// and the heat source Q; the adjoints sum |f*| or |g*|
+int phase_nv(int ph) { return ph == PH_FLOW || ph == PH_THERM ? 2 : 1; }
 
 // enqueue one step of a phase on stream s; the reducing variant writes the
 // per-block partial sums (and the fields of the post-boundary state)
@@ -302,8 +312,11 @@ lbm_status run_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, long long* ste
         cur = c->hres[0] / denom;
         if (ph == PH_FLOW)
             c->J_p = c->n_in > 0 ? c->obj.w_pin * c->hres[1] / (3.0 * (double)c->n_in) : 0.0;
-        if (ph == PH_THERM) c->J_T = c->obj.w_tmean * cur;
-        if (!std::isfinite(cur) || (ph == PH_FLOW && !std::isfinite(c->hres[1]))) {
+        if (ph == PH_THERM) {
+            c->J_T = c->obj.w_tmean * cur;
+            c->J_Q = -c->obj.w_qgen * c->hres[1];  // Eq. 72: J_Q = -sum Q
+        }
+        if (!std::isfinite(cur) || (phase_nv(ph) > 1 && !std::isfinite(c->hres[1]))) {
             *steps_out = steps;
             *res_out = NAN;
             *I_out = cur;
@@ -335,7 +348,7 @@ lbm_status ready(lbm_ctx* c) {
     if (!c) return fail(LBM_ERR_ARG, "ctx is null");
     if (!c->have_flags) return fail(LBM_ERR_ORDER, "lbm_set_flags has not been called");
     if (!c->have_gamma) return fail(LBM_ERR_ORDER, "lbm_set_gamma has not been called");
-    if (!c->have_bc) return fail(LBM_ERR_ORDER, "lbm_set_bc_values has not been called");
+    if (!c->have_bc) return fail(LBM_ERR_ORDER, "boundary values have not been set (lbm_set_bc_values / lbm_set_bc)");
     if (!c->have_params) return fail(LBM_ERR_ORDER, "lbm_set_params has not been called");
     return LBM_OK;
 }
@@ -391,7 +404,7 @@ lbm_status copy_out(lbm_ctx* c, void* dst, const void* src, int nplanes, int dty
     return LBM_OK;
 }
 
-lbm_status init_forward(lbm_ctx* c) {
+lbm_status init_flow(lbm_ctx* c) {
     FlowLaunch a = flow_base(c);
     a.fout = c->f[0];
     a.out0 = c->rho;
@@ -399,34 +412,124 @@ lbm_status init_forward(lbm_ctx* c) {
     c->fcur = 0;
     CUDA_TRY(flow_launch(c->stencil, c->storage, FOP_INIT_F, a, c->geom, c->stream));
     c->last_I[PH_FLOW] = 0.0;
-    if (c->thermal) {
-        ThermLaunch t = therm_base(c);
-        t.gout = c->g[0];
-        t.out0 = c->T;
-        t.out1 = c->gpost;
-        c->gcur = 0;
-        CUDA_TRY(thermal_launch(c->storage, TOP_INIT_G, t, c->geom, c->stream));
-        c->last_I[PH_THERM] = c->prm.T0;
-    }
     return LBM_OK;
 }
 
-lbm_status init_adjoint(lbm_ctx* c) {
+lbm_status init_temperature(lbm_ctx* c) {
+    ThermLaunch t = therm_base(c);
+    t.gout = c->g[0];
+    t.out0 = c->T;
+    t.out1 = c->gpost;
+    c->gcur = 0;
+    CUDA_TRY(thermal_launch(c->storage, TOP_INIT_G, t, c->geom, c->stream));
+    c->last_I[PH_THERM] = c->prm.T0;
+    return LBM_OK;
+}
+
+lbm_status init_forward(lbm_ctx* c) {
+    lbm_status st = init_flow(c);
+    if (st == LBM_OK && c->thermal) st = init_temperature(c);
+    return st;
+}
+
+lbm_status init_flow_adjoint(lbm_ctx* c) {
     FlowLaunch a = flow_base(c);
     a.aout = c->fa[0];
     c->facur = 0;
     CUDA_TRY(flow_launch(c->stencil, c->storage, FOP_INIT_A, a, c->geom, c->stream));
     c->last_I[PH_ADJ] = 0.0;
-    if (c->thermal) {
-        ThermLaunch t = therm_base(c);
-        t.aout = c->ga[0];
-        c->gacur = 0;
-        CUDA_TRY(thermal_launch(c->storage, TOP_INIT_A, t, c->geom, c->stream));
-        CUDA_TRY(cudaMemsetAsync(c->cpl, 0, 3 * c->np * c->rb, c->stream));
-        CUDA_TRY(cudaMemsetAsync(c->sT, 0, c->np * c->rb, c->stream));
-        c->last_I[PH_TADJ] = 0.0;
-    }
     return LBM_OK;
+}
+
+lbm_status init_temperature_adjoint(lbm_ctx* c) {
+    ThermLaunch t = therm_base(c);
+    t.aout = c->ga[0];
+    c->gacur = 0;
+    CUDA_TRY(thermal_launch(c->storage, TOP_INIT_A, t, c->geom, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->cpl, 0, 3 * c->np * c->rb, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sT, 0, c->np * c->rb, c->stream));
+    c->last_I[PH_TADJ] = 0.0;
+    return LBM_OK;
+}
+
+lbm_status init_adjoint(lbm_ctx* c) {
+    lbm_status st = init_flow_adjoint(c);
+    if (st == LBM_OK && c->thermal) st = init_temperature_adjoint(c);
+    return st;
+}
+
+// thermal-to-flow coupling and thermal sensitivity from the current
+// temperature adjoint iterate (run once the temperature adjoint has finished)
+lbm_status run_coupling(lbm_ctx* c) {
+    ThermLaunch t = therm_base(c);
+    t.gin = c->g[c->gcur];
+    t.ain = c->ga[c->gacur];
+    t.out0 = c->cpl;
+    t.out1 = c->sT;
+    CUDA_TRY(thermal_launch(c->storage, TOP_COUPLING, t, c->geom, c->stream));
+    return LBM_OK;
+}
+
+// One phase of the solve sequence flow -> temperature -> temperature adjoint
+// (+ coupling) -> flow adjoint, with its order checks and state bookkeeping.
+// do_reset restarts the phase's populations (the flow phase restarts the
+// temperature populations too, the temperature-adjoint phase the flow-adjoint
+// ones: a restarted phase invalidates the warm start of the phases after it).
+lbm_status solve_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, bool do_reset,
+                       long long* steps, double* res, double* I) {
+    *steps = 0;
+    *res = 0;
+    *I = 0;
+    lbm_status st = LBM_OK;
+    if (ph == PH_FLOW) {
+        if (do_reset || !c->fstate) {
+            if ((st = init_forward(c)) != LBM_OK) return st;
+            c->fstate = true;
+        }
+        c->flow_done = c->fwd_done = c->tadj_done = c->adj_done = false;
+    } else if (ph == PH_THERM) {
+        if (!c->flow_done) return fail(LBM_ERR_ORDER, "the temperature phase needs a completed flow phase");
+        if (do_reset && (st = init_temperature(c)) != LBM_OK) return st;
+        c->fwd_done = c->tadj_done = c->adj_done = false;
+    } else if (ph == PH_TADJ) {
+        if (!c->fwd_done) return fail(LBM_ERR_ORDER, "the temperature adjoint needs a completed forward solve");
+        if (do_reset || !c->astate) {
+            if ((st = init_adjoint(c)) != LBM_OK) return st;
+            c->astate = true;
+        }
+        c->tadj_done = c->adj_done = false;
+    } else {
+        if (!c->fwd_done) return fail(LBM_ERR_ORDER, "the flow adjoint needs a completed forward solve");
+        if (c->thermal && !c->tadj_done)
+            return fail(LBM_ERR_ORDER, "the flow adjoint needs a completed temperature adjoint");
+        if (!c->astate) {
+            if ((st = init_adjoint(c)) != LBM_OK) return st;
+            c->astate = true;
+        } else if (do_reset) {
+            if ((st = init_flow_adjoint(c)) != LBM_OK) return st;
+        }
+        c->adj_done = false;
+    }
+    st = run_phase(c, ph, o, steps, res, I);
+    if (st < 0) {
+        // a failed phase leaves no usable warm start for its lattice pair
+        if (ph == PH_FLOW || ph == PH_THERM) c->fstate = false;
+        else c->astate = false;
+        return st;
+    }
+    if (ph == PH_FLOW) {
+        c->flow_done = true;
+        c->fwd_done = !c->thermal;
+    } else if (ph == PH_THERM) {
+        c->fwd_done = true;
+    } else if (ph == PH_TADJ) {
+        lbm_status s2 = run_coupling(c);
+        if (s2 != LBM_OK) return s2;
+        c->tadj_done = true;
+    } else {
+        c->adj_done = true;
+    }
+    return st;
 }
 
 double now_ms() {
@@ -530,6 +633,7 @@ lbm_status lbm_create(lbm_ctx** out, int stencil, int nx, int ny, int nz, int st
 
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
+    if (c->holder) batch_forget(c->holder, c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_all(c);
@@ -567,6 +671,7 @@ lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_devi
     }
     CUDA_TRY(cudaMemcpyAsync(c->flags, h.data(), n, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->hflags.swap(h);
     // the captured step graphs read the flags from device memory, but their
     // objective source terms are baked from N_in and N_nonwall: recapture only
     // when those counts change
@@ -575,6 +680,7 @@ lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_devi
     c->n_nw = nnw;
     c->have_flags = true;
     c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     c->fstate = c->astate = false;
     return leave(c);
 }
@@ -589,6 +695,7 @@ lbm_status lbm_set_gamma(lbm_ctx* c, const void* gamma, size_t n, int dtype, int
     if (st != LBM_OK) return st;
     c->have_gamma = true;
     c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     return leave(c);
 }
 
@@ -602,6 +709,7 @@ lbm_status lbm_set_bc_values(lbm_ctx* c, const void* v, size_t n, int dtype, int
     if (st != LBM_OK) return st;
     c->have_bc = true;
     c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     return leave(c);
 }
 
@@ -614,26 +722,133 @@ lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
     if (c->thermal && !(p->kappa_f >= 0)) return fail(LBM_ERR_ARG, "kappa_f must be >= 0");
     if (c->thermal && !(p->k_ratio > 0)) return fail(LBM_ERR_ARG, "k_ratio must be > 0");
     if (!std::isfinite(p->q_flux) || !std::isfinite(p->T0)) return fail(LBM_ERR_ARG, "non-finite q_flux / T0");
+    if (!(p->beta_max >= 0) || !std::isfinite(p->beta_max)) return fail(LBM_ERR_ARG, "beta_max must be >= 0");
+    if (p->beta_max != 0 && !c->thermal) return fail(LBM_ERR_ARG, "beta_max needs the thermal lattice");
     // the captured graphs bake these values into their launches: recapture
     // only when one of them changes
     const lbm_params& q = c->prm;
     const bool same = c->have_params && q.tau == p->tau && q.rho0 == p->rho0 &&
                       q.gamma_model == p->gamma_model && q.kappa_f == p->kappa_f &&
-                      q.k_ratio == p->k_ratio && q.q_flux == p->q_flux && q.T0 == p->T0;
+                      q.k_ratio == p->k_ratio && q.q_flux == p->q_flux && q.T0 == p->T0 &&
+                      q.beta_max == p->beta_max;
     if (!same) c->drop_graphs();
     c->prm = *p;
     c->have_params = true;
     c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     return LBM_OK;
 }
 
 lbm_status lbm_set_objective(lbm_ctx* c, const lbm_objective* o) {
     if (!c || !o) return fail(LBM_ERR_ARG, "null argument");
-    if (!std::isfinite(o->w_pin) || !std::isfinite(o->w_tmean)) return fail(LBM_ERR_ARG, "non-finite weights");
-    if (c->obj.w_pin != o->w_pin || c->obj.w_tmean != o->w_tmean) c->drop_graphs();
+    if (!std::isfinite(o->w_pin) || !std::isfinite(o->w_tmean) || !std::isfinite(o->w_qgen))
+        return fail(LBM_ERR_ARG, "non-finite weights");
+    if (o->w_qgen != 0 && !c->thermal) return fail(LBM_ERR_ARG, "w_qgen needs the thermal lattice");
+    if (c->obj.w_pin != o->w_pin || c->obj.w_tmean != o->w_tmean || c->obj.w_qgen != o->w_qgen)
+        c->drop_graphs();
     c->obj = *o;
-    c->adj_done = false;
+    c->adj_done = c->tadj_done = false;
     return LBM_OK;
+}
+
+lbm_status lbm_physics_to_params(const lbm_physics* ph, lbm_params* out) {
+    if (!ph || !out) return fail(LBM_ERR_ARG, "null argument");
+    const double vals[] = {ph->re, ph->u_ref, ph->l_ref, ph->dp, ph->pr, ph->rho0,
+                           ph->k_ratio, ph->q_flux, ph->T0, ph->beta_max};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(LBM_ERR_ARG, "non-finite physics value");
+    if (!(ph->re > 0)) return fail(LBM_ERR_ARG, "re must be > 0");
+    if (!(ph->l_ref > 0)) return fail(LBM_ERR_ARG, "l_ref must be > 0");
+    if (!(ph->rho0 > 0)) return fail(LBM_ERR_ARG, "rho0 must be > 0");
+    if (ph->pr < 0) return fail(LBM_ERR_ARG, "pr must be >= 0");
+    double U = ph->u_ref;
+    if (!(U > 0)) {
+        if (!(ph->dp > 0)) return fail(LBM_ERR_ARG, "needs u_ref > 0 or a pressure drop dp > 0");
+        U = std::sqrt(ph->dp / ph->rho0);  // Eq. 70
+    }
+    const double nu = U * ph->l_ref / ph->re;  // Re = U L / nu
+    lbm_params p;
+    p.tau = 0.5 + 3.0 * nu;                    // Eq. 3: nu = (tau - 1/2) c_s^2, c_s^2 = 1/3
+    p.rho0 = ph->rho0;
+    p.gamma_model = ph->gamma_model;
+    p.kappa_f = ph->pr > 0 ? nu / ph->pr : 0.0;
+    p.k_ratio = ph->k_ratio;
+    p.q_flux = ph->q_flux;
+    p.T0 = ph->T0;
+    p.beta_max = ph->beta_max;
+    *out = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_physics(lbm_ctx* c, const lbm_physics* ph) {
+    if (!c || !ph) return fail(LBM_ERR_ARG, "null argument");
+    if (c->thermal && !(ph->pr > 0)) return fail(LBM_ERR_ARG, "pr must be > 0 with the thermal lattice");
+    lbm_params p;
+    lbm_status st = lbm_physics_to_params(ph, &p);
+    if (st != LBM_OK) return st;
+    return lbm_set_params(c, &p);
+}
+
+lbm_status lbm_set_bc(lbm_ctx* c, int face, int kind, const void* values, size_t n, int dtype,
+                      int on_device) {
+    if (!c || !values) return fail(LBM_ERR_ARG, "null argument");
+    if (face < 0 || face > 5) return fail(LBM_ERR_ARG, "face must be 0..5");
+    if (c->stencil == LBM_D2Q9 && face > 3) return fail(LBM_ERR_ARG, "D2Q9 lattices have faces 0..3");
+    if (kind != LBM_VEL && kind != LBM_PRES) return fail(LBM_ERR_ARG, "kind must be LBM_VEL or LBM_PRES");
+    if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(LBM_ERR_ARG, "bad dtype");
+    if (!c->have_flags) return fail(LBM_ERR_ORDER, "lbm_set_flags has not been called");
+    // the face as a 2-D block of nodes: start node, row width, row pitch, rows
+    const long long nx = c->nx, ny = c->ny, nz = c->nz;
+    const int ax = face >> 1, hi = face & 1;
+    long long start = 0, width = 0, pitch = 0, rows = 0;
+    if (ax == 0) { start = hi ? nx - 1 : 0; width = 1; pitch = nx; rows = ny * nz; }
+    else if (ax == 1) { start = hi ? nx * (ny - 1) : 0; width = nx; pitch = nx * ny; rows = nz; }
+    else { start = hi ? nx * ny * (nz - 1) : 0; width = nx * ny; pitch = nx * ny; rows = 1; }
+    std::vector<long long> slot;  // position in the face block of each matching node, node order
+    for (long long r = 0; r < rows; ++r)
+        for (long long w = 0; w < width; ++w) {
+            const uint8_t fl = c->hflags[start + r * pitch + w];
+            if ((fl & 7) == kind && ((fl >> 3) & 7) == face) slot.push_back(r * width + w);
+        }
+    const size_t m = slot.size();
+    if (m == 0) return fail(LBM_ERR_ARG, "no node of this kind with this normal on the face");
+    if (n != 4 && n != 4 * m) return fail(LBM_ERR_ARG, "values: n must be 4 or 4 x the face's nodes of this kind");
+    std::vector<double> v(n);
+    const size_t eb = dtype == LBM_DTYPE_F64 ? 8 : 4;
+    std::vector<char> raw(n * eb);
+    lbm_status st = enter(c);
+    if (st != LBM_OK) return st;
+    if (on_device) {
+        CUDA_TRY(cudaMemcpyAsync(raw.data(), values, n * eb, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(raw.data(), values, n * eb);
+    }
+    for (size_t i = 0; i < n; ++i)
+        v[i] = eb == 8 ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(LBM_ERR_ARG, "non-finite boundary value");
+    // read the face block, write the matching nodes' four values, put it back
+    const size_t rb = c->rb, nb = 4 * rb;
+    std::vector<char> blk((size_t)(rows * width) * nb);
+    char* base = (char*)c->bc + (size_t)start * nb;
+    CUDA_TRY(cudaMemcpy2DAsync(blk.data(), width * nb, base, pitch * nb, width * nb, rows,
+                               cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < m; ++k)
+        for (int j = 0; j < 4; ++j) {
+            const double x = v[(n == 4 ? 0 : 4 * k) + j];
+            char* dst = blk.data() + (size_t)slot[k] * nb + j * rb;
+            if (rb == 8) *(double*)dst = x;
+            else *(float*)dst = (float)x;
+        }
+    CUDA_TRY(cudaMemcpy2DAsync(base, pitch * nb, blk.data(), width * nb, width * nb, rows,
+                               cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->have_bc = true;
+    c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
+    return leave(c);
 }
 
 lbm_status lbm_forward(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
@@ -642,30 +857,22 @@ lbm_status lbm_forward(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     if ((st = check_opts(o)) != LBM_OK) return st;
     double t0 = now_ms();
     if ((st = enter(c)) != LBM_OK) return st;
-    if (o->reset || !c->fstate) {
-        if ((st = init_forward(c)) != LBM_OK) return st;
-        c->fstate = true;
-    }
-    c->fwd_done = false;
-    c->adj_done = false;
     long long s1 = 0, s2 = 0;
     double res = 0, I = 0;
-    lbm_status st1 = run_phase(c, PH_FLOW, o, &s1, &res, &I);
+    lbm_status st1 = solve_phase(c, PH_FLOW, o, o->reset != 0, &s1, &res, &I);
     lbm_status st2 = LBM_OK;
     if (st1 >= 0 && c->thermal) {
         double r2 = 0, I2 = 0;
-        st2 = run_phase(c, PH_THERM, o, &s2, &r2, &I2);
+        st2 = solve_phase(c, PH_THERM, o, false, &s2, &r2, &I2);
         res = std::max(res, r2);
         I = I2;
     }
     lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
-    if (final >= 0) c->fwd_done = true;
-    else c->fstate = false;
     if (rep) {
         rep->steps = s1 + s2;
         rep->residual = res;
         rep->I = I;
-        rep->J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        rep->J = c->J();
         rep->ms = now_ms() - t0;
         rep->status = final;
     }
@@ -680,43 +887,50 @@ lbm_status lbm_adjoint(lbm_ctx* c, const lbm_solve_opts* o, lbm_report* rep) {
     if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_adjoint needs a completed lbm_forward");
     double t0 = now_ms();
     if ((st = enter(c)) != LBM_OK) return st;
-    if (o->reset || !c->astate) {
-        if ((st = init_adjoint(c)) != LBM_OK) return st;
-        c->astate = true;
-    }
-    c->adj_done = false;
     long long s1 = 0, s2 = 0;
     double res = 0, I = 0;
     lbm_status st1 = LBM_OK, st2 = LBM_OK;
-    if (c->thermal) {
-        st1 = run_phase(c, PH_TADJ, o, &s1, &res, &I);
-        if (st1 >= 0) {
-            ThermLaunch t = therm_base(c);
-            t.gin = c->g[c->gcur];
-            t.ain = c->ga[c->gacur];
-            t.out0 = c->cpl;
-            t.out1 = c->sT;
-            cudaError_t e = thermal_launch(c->storage, TOP_COUPLING, t, c->geom, c->stream);
-            if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-        }
-    }
+    if (c->thermal) st1 = solve_phase(c, PH_TADJ, o, o->reset != 0, &s1, &res, &I);
     if (st1 >= 0) {
         double r2 = 0, I2 = 0;
-        st2 = run_phase(c, PH_ADJ, o, &s2, &r2, &I2);
+        st2 = solve_phase(c, PH_ADJ, o, !c->thermal && o->reset != 0, &s2, &r2, &I2);
         res = std::max(res, r2);
         I = I2;
     }
     lbm_status final = st1 < 0 ? st1 : (st2 < 0 ? st2 : (st1 > 0 ? st1 : st2));
-    if (final >= 0) c->adj_done = true;
-    else c->astate = false;
     if (rep) {
         rep->steps = s1 + s2;
         rep->residual = res;
         rep->I = I;
-        rep->J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        rep->J = c->J();
         rep->ms = now_ms() - t0;
         rep->status = final;
     }
+    lbm_status lv = leave(c);
+    return final != LBM_OK ? final : lv;
+}
+
+lbm_status lbm_solve_phase(lbm_ctx* c, int phase, const lbm_solve_opts* o, lbm_report* rep) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if ((st = check_opts(o)) != LBM_OK) return st;
+    if (phase < PH_FLOW || phase > PH_TADJ) return fail(LBM_ERR_ARG, "unknown phase");
+    if ((phase == PH_THERM || phase == PH_TADJ) && !c->thermal)
+        return fail(LBM_ERR_ARG, "temperature phase without the thermal lattice");
+    double t0 = now_ms();
+    if ((st = enter(c)) != LBM_OK) return st;
+    long long steps = 0;
+    double res = 0, I = 0;
+    lbm_status final = solve_phase(c, phase, o, o->reset != 0, &steps, &res, &I);
+    if (rep) {
+        rep->steps = steps;
+        rep->residual = res;
+        rep->I = I;
+        rep->J = c->J();
+        rep->ms = now_ms() - t0;
+        rep->status = final;
+    }
+    if (final == LBM_ERR_ORDER || final == LBM_ERR_ARG) return final;
     lbm_status lv = leave(c);
     return final != LBM_OK ? final : lv;
 }
@@ -753,7 +967,7 @@ lbm_status lbm_get_fields(lbm_ctx* c, void* rho, void* u, void* T, int dtype, in
 lbm_status lbm_get_objective(lbm_ctx* c, double* J) {
     if (!c || !J) return fail(LBM_ERR_ARG, "null argument");
     if (!c->fwd_done) return fail(LBM_ERR_ORDER, "lbm_get_objective needs a completed lbm_forward");
-    *J = c->J_p + (c->thermal ? c->J_T : 0.0);
+    *J = c->J();
     return LBM_OK;
 }
 
@@ -785,7 +999,8 @@ struct StateHeader {
     int nx, ny, nz;
     long long np, n_in, n_nw;
     int fstate, astate, fwd_done, adj_done;
-    double J_p, J_T;
+    int flow_done, tadj_done;
+    double J_p, J_T, J_Q;
     double last_I[4];
     double tau, rho0;
 };
@@ -836,7 +1051,7 @@ lbm_status lbm_export_state(lbm_ctx* c, void* dst, size_t bytes) {
     StateHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "LBMSTATE", 8);
-    h.version = 1;
+    h.version = 2;
     h.stencil = c->stencil;
     h.storage = c->storage;
     h.thermal = c->thermal;
@@ -850,8 +1065,11 @@ lbm_status lbm_export_state(lbm_ctx* c, void* dst, size_t bytes) {
     h.astate = c->astate;
     h.fwd_done = c->fwd_done;
     h.adj_done = c->adj_done;
+    h.flow_done = c->flow_done;
+    h.tadj_done = c->tadj_done;
     h.J_p = c->J_p;
     h.J_T = c->J_T;
+    h.J_Q = c->J_Q;
     for (int k = 0; k < 4; ++k) h.last_I[k] = c->last_I[k];
     h.tau = c->prm.tau;
     h.rho0 = c->prm.rho0;
@@ -874,7 +1092,7 @@ lbm_status lbm_import_state(lbm_ctx* c, const void* src, size_t bytes) {
     StateHeader h;
     CUDA_TRY(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 2)
         return fail(LBM_ERR_ARG, "not a state written by lbm_export_state");
     if (h.stencil != c->stencil || h.storage != c->storage || h.thermal != (int)c->thermal ||
         h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.np != c->np)
@@ -895,8 +1113,11 @@ lbm_status lbm_import_state(lbm_ctx* c, const void* src, size_t bytes) {
     c->astate = h.astate;
     c->fwd_done = h.fwd_done;
     c->adj_done = h.adj_done;
+    c->flow_done = h.flow_done;
+    c->tadj_done = h.tadj_done;
     c->J_p = h.J_p;
     c->J_T = h.J_T;
+    c->J_Q = h.J_Q;
     for (int k = 0; k < 4; ++k) c->last_I[k] = h.last_I[k];
     return leave(c);
 }
@@ -987,12 +1208,24 @@ struct lbm_batch {
     std::vector<std::pair<int, lbm_report>> done;
     bool dirty = true;
     std::map<int, cudaGraphExec_t> graphs;
+    size_t budget = 0;                 // device bytes the counted contexts may hold (0: no limit)
+    std::map<lbm_ctx*, size_t> held;   // counted contexts and their footprints
+    size_t held_bytes = 0;
 };
 
 namespace {
 
 // the __constant__ bank of a storage type serves one live batch at a time
 bool g_bank_busy[4] = {false, false, false, false};
+
+void batch_forget(lbm_batch* b, lbm_ctx* c) {
+    auto it = b->held.find(c);
+    if (it != b->held.end()) {
+        b->held_bytes -= it->second;
+        b->held.erase(it);
+    }
+    c->holder = nullptr;
+}
 
 void batch_slot_refresh(lbm_batch* b, int i) {
     BatchEntry& en = b->e[i];
@@ -1088,6 +1321,7 @@ lbm_status batch_advance(lbm_batch* b, int i, int st) {
     } else {
         if (st > 0 && en.status == LBM_OK) en.status = st;
         if (en.phase == SP_FLOW) {
+            c->flow_done = true;
             if (c->thermal) {
                 en.phase = SP_THERM;
             } else {
@@ -1098,12 +1332,9 @@ lbm_status batch_advance(lbm_batch* b, int i, int st) {
             c->fwd_done = true;
             en.phase = c->thermal ? SP_TADJ : SP_ADJ;
         } else if (en.phase == SP_TADJ) {
-            ThermLaunch t = therm_base(c);
-            t.gin = c->g[c->gcur];
-            t.ain = c->ga[c->gacur];
-            t.out0 = c->cpl;
-            t.out1 = c->sT;
-            CUDA_TRY(thermal_launch(c->storage, TOP_COUPLING, t, c->geom, c->stream));
+            lbm_status s2 = run_coupling(c);
+            if (s2 != LBM_OK) return s2;
+            c->tadj_done = true;
             en.phase = SP_ADJ;
         } else if (en.phase == SP_ADJ) {
             c->adj_done = true;
@@ -1129,7 +1360,7 @@ lbm_status batch_advance(lbm_batch* b, int i, int st) {
         r.steps = en.total;
         r.residual = en.res;
         r.I = c->last_I[PH_ADJ];
-        r.J = c->J_p + (c->thermal ? c->J_T : 0.0);
+        r.J = c->J();
         r.ms = now_ms() - en.t0;
         r.status = en.status;
         b->done.push_back(std::make_pair(i, r));
@@ -1156,7 +1387,8 @@ size_t lbm_footprint_bytes(int stencil, int nx, int ny, int nz, int storage, int
     return bytes;
 }
 
-lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots) {
+lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int max_slots,
+                            size_t hbm_budget_bytes) {
     if (!out) return fail(LBM_ERR_ARG, "out is null");
     *out = nullptr;
     if (storage == LBM_FP64) return fail(LBM_ERR_UNSUPPORTED, "batches are built for FP32 arithmetic storage");
@@ -1171,6 +1403,7 @@ lbm_status lbm_batch_create(lbm_batch** out, int storage, int check_every, int m
     b->storage = storage;
     b->K = check_every;
     b->max_slots = max_slots;
+    b->budget = hbm_budget_bytes;
     b->h_bank.assign(batch_bank_bytes(storage), 0);
     b->e.resize(max_slots);
     g_bank_busy[storage] = true;
@@ -1197,6 +1430,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : b->held) kv.first->holder = nullptr;
     for (int ph = 0; ph < 4; ++ph)
         if (b->d_tiles[ph]) cudaFree(b->d_tiles[ph]);
     g_bank_busy[b->storage] = false;
@@ -1222,6 +1456,15 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* c, const lbm_solve_opts* o, in
             break;
         }
     if (i < 0) return fail(LBM_ERR_ARG, "batch is full");
+    if (c->holder && c->holder != b) return fail(LBM_ERR_ARG, "context is counted by another batch");
+    size_t fp = 0;
+    if (c->holder != b) {
+        fp = lbm_footprint_bytes(c->stencil, c->nx, c->ny, c->nz, c->storage, c->thermal);
+        if (b->budget > 0 && b->held_bytes + fp > b->budget)
+            return fail(LBM_ERR_OOM, "context needs " + std::to_string(fp) + " bytes; the batch holds " +
+                                         std::to_string(b->held_bytes) + " of its " +
+                                         std::to_string(b->budget) + "-byte budget");
+    }
     if ((st = enter(c)) != LBM_OK) return st;
     if (o->reset || !c->fstate) {
         if ((st = init_forward(c)) != LBM_OK) return st;
@@ -1229,7 +1472,13 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* c, const lbm_solve_opts* o, in
     }
     if (o->reset) c->astate = false;
     c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->holder != b) {
+        b->held[c] = fp;
+        b->held_bytes += fp;
+        c->holder = b;
+    }
     BatchEntry& en = b->e[i];
     en = BatchEntry();
     en.ctx = c;
@@ -1307,10 +1556,13 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
             const double denom = (double)(c->n_nw > 0 ? c->n_nw : 1);
             const double cur = r[0] / denom;
             if (ph == SP_FLOW) c->J_p = c->n_in > 0 ? c->obj.w_pin * r[1] / (3.0 * (double)c->n_in) : 0.0;
-            if (ph == SP_THERM) c->J_T = c->obj.w_tmean * cur;
+            if (ph == SP_THERM) {
+                c->J_T = c->obj.w_tmean * cur;
+                c->J_Q = -c->obj.w_qgen * r[1];
+            }
             en.steps += b->K;
             en.total += b->K;
-            const bool bad = !std::isfinite(cur) || (ph == SP_FLOW && !std::isfinite(r[1]));
+            const bool bad = !std::isfinite(cur) || (ph <= SP_THERM && !std::isfinite(r[1]));
             if (bad) {
                 c->last_I[cph] = cur;
                 lbm_status st = batch_advance(b, i, LBM_ERR_DIVERGED);
@@ -1332,6 +1584,23 @@ lbm_status lbm_batch_step(lbm_batch* b, int* n_active) {
         for (int i = 0; i < b->max_slots; ++i) n += b->e[i].used && b->e[i].phase != SP_DONE;
         *n_active = n;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_release(lbm_batch* b, lbm_ctx* c) {
+    if (!b || !c) return fail(LBM_ERR_ARG, "null argument");
+    if (c->holder != b) return fail(LBM_ERR_ARG, "context is not counted by this batch");
+    for (int i = 0; i < b->max_slots; ++i)
+        if (b->e[i].used && b->e[i].ctx == c)
+            return fail(LBM_ERR_ORDER, "context is still in the batch (running or not yet polled)");
+    batch_forget(b, c);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_memory(lbm_batch* b, size_t* budget, size_t* held) {
+    if (!b) return fail(LBM_ERR_ARG, "batch is null");
+    if (budget) *budget = b->budget;
+    if (held) *held = b->held_bytes;
     return LBM_OK;
 }
 

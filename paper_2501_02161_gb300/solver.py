@@ -29,15 +29,19 @@ class Report:
 
 
 def _ptr(x):
-    """(pointer, on_device, dtype code) for a torch tensor or numpy array."""
+    """(pointer, on_device, dtype code, owner) for a torch tensor or an array-like;
+    keep `owner` alive until the call that uses the pointer returns."""
     if isinstance(x, torch.Tensor):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if x.dtype not in (torch.float64, torch.float32):
+            raise ValueError("tensor must be float64 or float32")
         dt = C.LBM_DTYPE_F64 if x.dtype == torch.float64 else C.LBM_DTYPE_F32
-        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), dt
-    x = np.ascontiguousarray(x)
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), dt, x
+    x = np.asarray(x)
+    x = np.ascontiguousarray(x, dtype=x.dtype if x.dtype in (np.float32, np.float64) else np.float64)
     dt = C.LBM_DTYPE_F64 if x.dtype == np.float64 else C.LBM_DTYPE_F32
-    return ctypes.c_void_p(x.ctypes.data), 0, dt
+    return ctypes.c_void_p(x.ctypes.data), 0, dt, x
 
 
 class Solver:
@@ -61,17 +65,27 @@ class Solver:
 
     @classmethod
     def from_lattice(cls, lat, storage: str = "fp32", device=None) -> "Solver":
-        if getattr(lat, "beta_max", 0.0) != 0.0 or getattr(lat, "w_qgen", 0.0) != 0.0:
-            raise NotImplementedError("heat generation in the solid (beta_max, w_qgen; Eq. 69-72) "
-                                      "is not built in the CUDA solver")
         s = cls(lat.stencil, lat.nx, lat.ny, lat.nz, storage, lat.thermal, device)
         s.set_flags(torch.as_tensor(lat.flags, dtype=torch.uint8, device=s.device))
         s.set_gamma(torch.as_tensor(lat.gamma, dtype=s.rdtype, device=s.device))
         s.set_bc_values(torch.as_tensor(lat.bcval, dtype=s.rdtype, device=s.device))
-        s.set_params(tau=lat.tau, rho0=lat.rho0, gamma_model=lat.gamma_model,
-                     kappa_f=lat.kappa_f, k_ratio=lat.k_ratio, q_flux=lat.q_flux, T0=lat.T0)
-        s.set_objective(lat.w_pin, lat.w_tmean)
+        s.set_lattice_params(lat)
         return s
+
+    def set_lattice_params(self, lat):
+        """The lattice's physical parameters and objective weights: through
+        lbm_set_physics when it is specified by Re (and Pr), else through
+        lbm_set_params with its tau (and kappa_f)."""
+        if lat.re is not None:
+            self.set_physics(re=lat.re, u_ref=lat.u_ref, l_ref=lat.l_ref, dp=lat.dp,
+                             pr=lat.pr or 0.0, rho0=lat.rho0, gamma_model=lat.gamma_model,
+                             k_ratio=lat.k_ratio, q_flux=lat.q_flux, T0=lat.T0,
+                             beta_max=lat.beta_max)
+        else:
+            self.set_params(tau=lat.tau, rho0=lat.rho0, gamma_model=lat.gamma_model,
+                            kappa_f=lat.kappa_f or 0.0, k_ratio=lat.k_ratio, q_flux=lat.q_flux,
+                            T0=lat.T0, beta_max=lat.beta_max)
+        self.set_objective(lat.w_pin, lat.w_tmean, lat.w_qgen)
 
     def close(self):
         if self._ctx:
@@ -100,22 +114,39 @@ class Solver:
         C.check(self.lib.lbm_set_flags(self._ctx, p, self.N, dev), "lbm_set_flags")
 
     def set_gamma(self, gamma):
-        p, dev, dt = _ptr(gamma)
+        p, dev, dt, _keep = _ptr(gamma)
         self._stream()
         C.check(self.lib.lbm_set_gamma(self._ctx, p, self.N, dt, dev), "lbm_set_gamma")
 
     def set_bc_values(self, values):
-        p, dev, dt = _ptr(values)
+        p, dev, dt, _keep = _ptr(values)
         self._stream()
         C.check(self.lib.lbm_set_bc_values(self._ctx, p, 4 * self.N, dt, dev), "lbm_set_bc_values")
 
-    def set_params(self, tau, rho0=1.0, gamma_model=0, kappa_f=0.0, k_ratio=1.0, q_flux=0.0, T0=0.0):
-        prm = C.lbm_params(tau, rho0, gamma_model, kappa_f, k_ratio, q_flux, T0)
+    def set_params(self, tau, rho0=1.0, gamma_model=0, kappa_f=0.0, k_ratio=1.0, q_flux=0.0, T0=0.0,
+                   beta_max=0.0):
+        prm = C.lbm_params(tau, rho0, gamma_model, kappa_f, k_ratio, q_flux, T0, beta_max)
         C.check(self.lib.lbm_set_params(self._ctx, ctypes.byref(prm)), "lbm_set_params")
 
-    def set_objective(self, w_pin=1.0, w_tmean=0.0):
-        o = C.lbm_objective(w_pin, w_tmean)
+    def set_physics(self, re, u_ref=0.0, l_ref=1.0, dp=0.0, pr=0.0, rho0=1.0, gamma_model=0,
+                    k_ratio=1.0, q_flux=0.0, T0=0.0, beta_max=0.0):
+        """Parameters from Re = U L / nu and Pr = nu / kappa_f (Eq. 3; Eq. 70 when
+        the velocity scale is given by a pressure drop dp)."""
+        ph = C.lbm_physics(re, u_ref, l_ref, dp, pr, rho0, gamma_model, k_ratio, q_flux, T0,
+                           beta_max)
+        C.check(self.lib.lbm_set_physics(self._ctx, ctypes.byref(ph)), "lbm_set_physics")
+
+    def set_objective(self, w_pin=1.0, w_tmean=0.0, w_qgen=0.0):
+        o = C.lbm_objective(w_pin, w_tmean, w_qgen)
         C.check(self.lib.lbm_set_objective(self._ctx, ctypes.byref(o)), "lbm_set_objective")
+
+    def set_bc(self, face: int, kind: int, values):
+        """Boundary values of the VEL or PRES nodes on one face of the box
+        (4 numbers, or 4 per such node in node order)."""
+        p, dev, dt, keep = _ptr(values)
+        n = keep.numel() if isinstance(keep, torch.Tensor) else keep.size
+        self._stream()
+        C.check(self.lib.lbm_set_bc(self._ctx, int(face), int(kind), p, int(n), dt, dev), "lbm_set_bc")
 
     # ---- solves -------------------------------------------------------------
     def _solve(self, fn, name, tol, max_steps, check_every, reset, strict) -> Report:
@@ -140,11 +171,18 @@ class Solver:
         return self._solve(self.lib.lbm_adjoint, "lbm_adjoint", tol, max_steps, check_every,
                            reset, strict)
 
+    def solve_phase(self, phase: int, tol=1e-6, max_steps=20000, check_every=1000, reset=True,
+                    strict=True) -> Report:
+        """One phase of the solve sequence (0 flow, 1 temperature, 2 flow adjoint,
+        3 temperature adjoint; see lbm_solve_phase)."""
+        fn = lambda ctx, o, r: self.lib.lbm_solve_phase(ctx, int(phase), o, r)
+        return self._solve(fn, "lbm_solve_phase", tol, max_steps, check_every, reset, strict)
+
     def sensitivity(self, out: torch.Tensor | None = None, dtype=None) -> torch.Tensor:
         dtype = dtype or self.rdtype
         if out is None:
             out = torch.empty(self.N, dtype=dtype, device=self.device)
-        p, dev, dt = _ptr(out)
+        p, dev, dt, _keep = _ptr(out)
         self._stream()
         C.check(self.lib.lbm_sensitivity(self._ctx, p, dt, dev), "lbm_sensitivity")
         return out

@@ -1,0 +1,127 @@
+"""Converged FP32 solves against the FP64 oracle at equal step counts.
+
+The CUDA path runs every phase of the solve sequence (flow, temperature,
+temperature adjoint, flow adjoint) in FP32 to the workload's stopping rule
+(relative change of the residual quantity below 1e-6 over K = 1000 steps,
+Sec. 3.1); the oracle then runs exactly the same number of steps of each
+phase in FP64, and the converged fields are compared node by node.  Equal
+step counts separate FP32 rounding from the distance to the fixed point
+(two solves stopped by a residual rule at different steps differ by the
+iterations between them, not by rounding).  Bounds are the workload's:
+rel-L2 <= 1e-5 on rho, u, T and J, <= 1e-4 on dJ/dgamma, f* and g*.
+
+The full-size 128x64x32 heat sink (tens of thousands of steps per phase,
+about an hour of FP64 oracle time) runs only with LBM_LONG_TESTS=1.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2501_02161_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_STOP, K = 1e-6, 1000
+BOUND_FIELD, BOUND_ADJ = 1e-5, 1e-4
+RESULTS = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_02161_gb300 import build as B
+    B.build()
+    O.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def gpu_converged(lat, storage="fp32"):
+    """Each phase to the stopping rule; returns the fields and per-phase steps."""
+    from paper_2501_02161_gb300.solver import Solver
+    s = Solver.from_lattice(lat, storage=storage)
+    phases = [0, 1, 3, 2] if lat.thermal else [0, 2]
+    steps = {}
+    for ph in phases:
+        r = s.solve_phase(ph, tol=TOL_STOP, max_steps=400000, check_every=K)
+        assert r.status == 0, (ph, r)
+        steps[ph] = r.steps
+    rho, u, T = s.fields(torch.float64)
+    fs, gs = s.adjoint_fields(torch.float64)
+    out = dict(rho=rho.cpu().numpy(), u=u.cpu().numpy().T, J=s.objective(),
+               sens=s.sensitivity(dtype=torch.float64).cpu().numpy(), fs=fs.cpu().numpy().T)
+    if T is not None:
+        out["T"] = T.cpu().numpy()
+        out["gs"] = gs.cpu().numpy().T
+    s.close()
+    return out, steps
+
+
+def oracle_replay(lat, steps):
+    """The FP64 oracle, each phase run for the CUDA path's step count."""
+    orc = O.Oracle(lat)
+    orc.flow_run(steps[0])
+    out = {}
+    if lat.thermal:
+        orc.thermal_run(steps[1])
+        out["T"] = orc.temperature()
+        orc.thermal_adjoint_run(steps[3])
+        orc.finish_thermal_adjoint()
+        out["gs"] = orc.thermal_adjoint_post_bc().reshape(orc.N, 7)
+    orc.adjoint_run(steps[2])
+    rho, u = orc.macro()
+    out.update(rho=rho, u=u, J=orc.objective(), sens=orc.sensitivity(),
+               fs=orc.adjoint_post_bc().reshape(orc.N, orc.Q))
+    return out
+
+
+def check(lat, name):
+    g, steps = gpu_converged(lat)
+    o = oracle_replay(lat, steps)
+    keys = ("rho", "u", "sens", "fs") + (("T", "gs") if lat.thermal else ())
+    errs = {k: rel(g[k], o[k]) for k in keys}
+    errs["J"] = abs(g["J"] - o["J"]) / abs(o["J"])
+    RESULTS[name] = {"steps": {str(k): v for k, v in steps.items()}, "rel_l2": errs}
+    out = os.environ.get("LBM_TEST_RECORDS")  # optional folder for the measured values
+    if out and os.path.isdir(out):
+        json.dump(RESULTS, open(os.path.join(out, "converged_errors.json"), "w"), indent=1)
+    for k in ("rho", "u", "T", "J"):
+        if k in errs:
+            assert errs[k] <= BOUND_FIELD, errs
+    for k in ("sens", "fs", "gs"):
+        if k in errs:
+            assert errs[k] <= BOUND_ADJ, errs
+
+
+def test_pipe_bend_32cubed_re50_converged():
+    check(I.pipe_bend_3d(n=32, re=50.0, seed=1), "pipe_bend_32^3_re50")
+
+
+def test_heat_sink_32x16x12_converged():
+    check(I.heat_sink(nx=32, ny=16, nz=12, re=10.0, seed=4), "heat_sink_32x16x12_re10")
+
+
+def test_pipe_bend_64cubed_re50_converged():
+    """The 64^3 D3Q19 FP32 pipe bend at Re 50, full size, converged."""
+    check(I.pipe_bend_3d(n=64, re=50.0, seed=1), "pipe_bend_64^3_re50")
+
+
+@pytest.mark.skipif(os.environ.get("LBM_LONG_TESTS") != "1", reason="long: set LBM_LONG_TESTS=1")
+def test_pipe_bend_64cubed_re100_converged():
+    check(I.pipe_bend_3d(n=64, re=100.0, seed=1), "pipe_bend_64^3_re100")
+
+
+@pytest.mark.skipif(os.environ.get("LBM_LONG_TESTS") != "1", reason="long: set LBM_LONG_TESTS=1")
+def test_heat_sink_128x64x32_converged():
+    check(I.heat_sink(re=50.0, seed=4), "heat_sink_128x64x32_re50")
