@@ -144,13 +144,28 @@ def rel_change(a: float, b: float) -> float:
     return d / abs(a) if a != 0.0 else float("inf")
 
 
+def relaxation_of(lat):
+    """(tau, kappa_f) of a lattice: as given, or from its Reynolds and Prandtl
+    numbers.  Sec. 2.1, Eq. 3: nu = (tau - 1/2) c_s^2 with c_s^2 = 1/3, and
+    Re = U L / nu; the velocity scale U is the given one, or sqrt(dp / rho0)
+    for a pressure drop dp (Eq. 70); Pr = nu / kappa_f."""
+    if lat.re is None:
+        return lat.tau, lat.kappa_f
+    U = lat.u_ref if lat.u_ref > 0 else float(np.sqrt(lat.dp / lat.rho0))
+    nu = U * lat.l_ref / lat.re
+    tau = nu / (1.0 / 3.0) + 0.5
+    kappa_f = nu / lat.pr if lat.pr else 0.0
+    return tau, kappa_f
+
+
 class Oracle:
     """FP64 forward / adjoint / sensitivity on one synthetic lattice."""
 
     def __init__(self, lat):
         self.lat = lat
-        self.P = make_problem(lat.stencil, lat.nx, lat.ny, lat.nz, lat.tau, lat.rho0,
-                              lat.gamma_model, lat.thermal, lat.kappa_f, lat.k_ratio,
+        tau, kappa_f = relaxation_of(lat)
+        self.P = make_problem(lat.stencil, lat.nx, lat.ny, lat.nz, tau, lat.rho0,
+                              lat.gamma_model, lat.thermal, kappa_f, lat.k_ratio,
                               lat.q_flux, lat.w_pin, lat.w_tmean, lat.beta_max, lat.w_qgen)
         self.Q = 9 if lat.stencil == 0 else 19
         self.N = lat.n

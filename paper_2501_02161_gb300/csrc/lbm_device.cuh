@@ -218,6 +218,8 @@ struct ThermArgs {
     R rho0, kappa_f, k_ratio, q, T0;
     R src_T;                         // w_tmean / N_nonwall
     R ascale;
+    R beta;                          // beta_max: heat source Q = beta (1 - gamma)(1 - T) (Eq. 69)
+    R src_q;                         // w_qgen beta_max: -dJ_Q/dg_l = -src_q (1 - gamma)
 };
 
 // ---------------------------------------------------------------------------
@@ -768,8 +770,11 @@ __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const 
     return fl;
 }
 
+// collision with the heat source w_k Q, Q = beta_max (1 - gamma)(1 - T)
+// (Eq. 69, 71); the reducing step also sums T (residual, mean-T objective)
+// and Q (heat-generation objective, Eq. 72) over non-wall nodes
 template <typename T, typename TA, typename R, bool REDUCE>
-__device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
+__device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
     R g[7], gam, u0, u1, u2;
     const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
     using X = Ex<R>;
@@ -782,13 +787,17 @@ __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, 
         for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + c.n] = g[k];
     }
     if ((fl & 7) != WALL) {
-        if (REDUCE) acc[0] = (double)tem;
+        const R qs = X::mul(X::mul(a.beta, X::sub(R(1), gam)), X::sub(R(1), tem));
+        if (REDUCE) {
+            acc[0] = (double)tem;
+            acc[1] = (double)qs;
+        }
         const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
         const R g4 = X::mul(R(4), gam);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
             const R geq = X::mul(X::mul(R(D3Q7::w(k)), tem), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1)));
-            g[k] = X::fma(om, X::sub(geq, g[k]), g[k]);
+            g[k] = X::fma(R(D3Q7::w(k)), qs, X::fma(om, X::sub(geq, g[k]), g[k]));
         }
     }
 #pragma unroll
@@ -801,9 +810,9 @@ __global__ void __launch_bounds__(256) k_thermal_step(ThermArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
-    double acc[1] = {0.0};
+    double acc[2] = {0.0, 0.0};
     if (c.active) thermal_step_node<T, TA, R, REDUCE>(a, c, acc);
-    if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
+    if (REDUCE) block_partials<2>(acc, a.partials, grid_block_id());
 }
 
 template <typename T, typename TA, typename R>
@@ -827,16 +836,22 @@ __global__ void k_thermal_init(ThermArgs<T, TA, R> a, int which) {
 }
 
 // adjoint of the thermal collision at one node:
-//   g*_C,l = (1 - 1/tau_g) g*_S,l + (1/tau_g) sum_k w_k a_k g*_S,k - dJ/dg_l
+//   g*_C,l = (1 - 1/tau_g) g*_S,l + (1/tau_g) sum_k w_k a_k g*_S,k
+//            - beta_max (1 - gamma) sum_k w_k g*_S,k - dJ/dg_l
+// (the source w_k Q of Eq. 71 has dQ/dg_l = -beta_max (1 - gamma))
 template <typename R>
-__device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, R u1, R u2, R om, R src) {
+__device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, R u1, R u2, R om, R src,
+                                                        R beta) {
     using X = Ex<R>;
-    R B = 0;
+    R B = 0, W = 0;
     const R g4 = X::mul(R(4), gam);
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 7; ++k) {
         B = X::fma(X::mul(R(D3Q7::w(k)), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1))), s[k], B);
-    const R base = X::fma(om, B, -src);
+        W = X::fma(R(D3Q7::w(k)), s[k], W);
+    }
+    const R bg = X::mul(beta, X::sub(R(1), gam));
+    const R base = X::fma(om, B, X::fma(-bg, W, -src));
     const R om1 = X::sub(R(1), om);
 #pragma unroll
     for (int k = 0; k < 7; ++k) s[k] = X::fma(om1, s[k], base);
@@ -862,7 +877,9 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
         const R gam = a.gamma[c.n];
         const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
         const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
-        thermal_adjoint_collide<R>(s, gam, u0, u1, u2, om, a.src_T);
+        // -dJ/dg_l: mean-T objective and heat-generation objective (Eq. 72)
+        const R src = Ex<R>::fma(a.src_q, Ex<R>::sub(R(1), gam), a.src_T);
+        thermal_adjoint_collide<R>(s, gam, u0, u1, u2, om, src, a.beta);
         if (type >= VEL) {
             const int kn = ((fl >> 3) & 7) + 1;
             R ckn = 0, en = 0;
@@ -934,13 +951,14 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
         const R tg = tau_g<R>(gam, a.kappa_f, a.k_ratio);
         const R om = R(1) / tg;
         const R dom = -R(4) * a.kappa_f * (R(1) - a.k_ratio) * om * om;  // d(1/tau_g)/d gamma
-        R Mg0 = 0, Mg1 = 0, Mg2 = 0, s1 = 0;
+        R Mg0 = 0, Mg1 = 0, Mg2 = 0, s1 = 0, W = 0;
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
             const R ws = R(D3Q7::w(k)) * s[k];
             Mg0 += R(D3Q7::cx(k)) * ws;
             Mg1 += R(D3Q7::cy(k)) * ws;
             Mg2 += R(D3Q7::cz(k)) * ws;
+            W += ws;
             const R eu = ecomp<R>(k, u0, u1, u2);
             const R geq = R(D3Q7::w(k)) * tem * (R(1) + R(4) * gam * eu);
             s1 += s[k] * (-(gp[k] - geq) * dom + om * R(D3Q7::w(k)) * tem * R(4) * eu);
@@ -949,7 +967,10 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
         v0 = cf * Mg0;
         v1 = cf * Mg1;
         v2 = cf * Mg2;
-        sT = -s1;
+        // heat source: d(w_k Q)/d gamma = -w_k beta_max (1 - T); and the
+        // direct part of J_Q = -w_qgen sum beta_max (1 - gamma)(1 - T)
+        const R omT = R(1) - tem;
+        sT = -s1 + a.beta * omT * W + a.src_q * omT;
         if (type == PRES) {
             const int kn = ((fl >> 3) & 7) + 1;
             R en = 0;
@@ -1048,13 +1069,15 @@ __global__ void __launch_bounds__(256, 4)
             const ThermArgs<TG, TA, R>& a = C.t[sl][par];
             c.active = in_tile && c.x < a.nx && c.y < a.ny;
             c.n = c.x + (long long)a.nx * (c.y + (long long)a.ny * c.z);
-            double acc[1] = {0.0};
             if (P == 1) {
+                double acc[2] = {0.0, 0.0};
                 if (c.active) thermal_step_node<TG, TA, R, REDUCE>(a, c, acc);
+                if (REDUCE) block_partials<2>(acc, a.partials, tl.w);
             } else {
+                double acc[1] = {0.0};
                 if (c.active) thermal_adjoint_node<TG, TA, R, REDUCE>(a, c, acc);
+                if (REDUCE) block_partials<1>(acc, a.partials, tl.w);
             }
-            if (REDUCE) block_partials<1>(acc, a.partials, tl.w);
         }
     }
 }
@@ -1094,7 +1117,7 @@ __device__ __forceinline__ void batch_finalize_slot(const BatchConst<T, TG, TA, 
     }
 }
 
-// the flow phase sums two values (|u| and inlet rho), the others one
+// the flow and temperature phases sum two values, the adjoints one
 template <typename T, typename TG, typename TA, typename R, class Bank>
 __global__ void __launch_bounds__(256) k_batch_finalize(const int* __restrict__ list,
                                                         const int* __restrict__ nlist,
@@ -1103,7 +1126,7 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const int* __restrict__ 
     const int n = *nlist;
     for (int q = blockIdx.x; q < n; q += gridDim.x) {
         const int slot = list[q];
-        if (C.phase[slot] == 0)
+        if (C.phase[slot] <= 1)  // flow: |u| and inlet rho; temperature: T and Q
             batch_finalize_slot<2, T, TG, TA, R, Bank>(C, slot, results);
         else
             batch_finalize_slot<1, T, TG, TA, R, Bank>(C, slot, results);

@@ -53,7 +53,7 @@ struct ThermLaunch {
     double* partials;
     int nx, ny, nz;
     long long np;
-    double rho0, kappa_f, k_ratio, q, T0, src_T, ascale;
+    double rho0, kappa_f, k_ratio, q, T0, src_T, ascale, beta, src_q;
 };
 
 enum FlowOp {

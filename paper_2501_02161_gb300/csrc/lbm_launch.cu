@@ -98,6 +98,8 @@ therm_args(const ThermLaunch& l) {
     a.T0 = (R)l.T0;
     a.src_T = (R)l.src_T;
     a.ascale = (R)l.ascale;
+    a.beta = (R)l.beta;
+    a.src_q = (R)l.src_q;
     return a;
 }
 

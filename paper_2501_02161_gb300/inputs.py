@@ -52,11 +52,20 @@ class Lattice:
     flags: np.ndarray          # uint8[N]
     gamma: np.ndarray          # float64[N]
     bcval: np.ndarray          # float64[N*4]
-    tau: float
+    tau: float | None = None   # relaxation time, when the problem gives it directly
     rho0: float = 1.0
     gamma_model: int = GAMMA_EQ12
     thermal: bool = False
-    kappa_f: float = 0.0       # fluid thermal diffusivity (lattice units)
+    kappa_f: float = 0.0       # fluid thermal diffusivity, when given directly (lattice units)
+    # the problem in physical terms instead of tau / kappa_f: Reynolds number
+    # Re = U L / nu with velocity scale u_ref (or a pressure drop dp) and length
+    # scale l_ref, and Prandtl number pr = nu / kappa_f; the solver and the
+    # oracle each turn these into tau and kappa_f
+    re: float | None = None
+    u_ref: float = 0.0
+    l_ref: float = 0.0
+    dp: float = 0.0
+    pr: float | None = None
     k_ratio: float = 1.0       # solid / fluid conductivity ratio
     q_flux: float = 0.0        # heat added per step at each HEAT wall node
     T0: float = 0.0            # initial temperature
@@ -144,12 +153,6 @@ def parabola(j: int, w: int) -> float:
     return 4.0 * s * (1.0 - s)
 
 
-def tau_from_re(re: float, umax: float, width: float) -> float:
-    """Re := u_max * W / nu with nu = (tau - 1/2)/3 (Eq. 3)."""
-    nu = umax * width / re
-    return 0.5 + 3.0 * nu
-
-
 # --------------------------------------------------------------------------
 # geometries
 # --------------------------------------------------------------------------
@@ -180,8 +183,7 @@ def pipe_bend_2d(nx: int = 64, ny: int = 64, width: int = 16, umax: float = 0.05
     gam[(flags & 7) == WALL] = 0.0
     lat = Lattice("pipe_bend_2d", D2Q9, nx, ny, 1, flags.ravel(), gam.ravel(),
                   bc.ravel(), tau=tau, gamma_model=gamma_model)
-    lat.meta.update(width=width, umax=umax,
-                    re=umax * width / ((tau - 0.5) / 3.0))
+    lat.meta.update(width=width, umax=umax)
     return lat
 
 
@@ -221,10 +223,9 @@ def pipe_bend_3d(n: int = 64, width: int | None = None, umax: float = 0.05,
     kind = flags & 7
     gam[(kind == VEL) | (kind == PRES)] = 1.0
     gam[kind == WALL] = 0.0
-    tau = tau_from_re(re, umax, w)
     lat = Lattice(f"pipe_bend_3d_{nx}x{ny}x{nz}", D3Q19, nx, ny, nz,
-                  flags.ravel(), gam.ravel(), bc.ravel(), tau=tau,
-                  gamma_model=gamma_model)
+                  flags.ravel(), gam.ravel(), bc.ravel(), gamma_model=gamma_model,
+                  re=re, u_ref=umax, l_ref=float(w))
     lat.meta.update(width=w, umax=umax, re=re, seed=seed)
     return lat
 
@@ -240,7 +241,8 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
     Inlet face x=0 and outlet face x=nx-1 over the interior cross-section
     (velocity inlet with a product parabola and T=0; fixed-density outlet).
     Walls on y=0, y=ny-1, z=0, z=nz-1; the z=0 wall under the interior is
-    heated with q_flux per node and step.  Re uses the smaller inlet side.
+    heated with q_flux per node and step.  Re uses the inlet's peak speed and
+    its smaller side; Pr sets the fluid diffusivity.
     The first and last `plenum` x-layers are fluid (gamma = 1).
     """
     flags = np.zeros((nz, ny, nx), np.uint8)
@@ -268,12 +270,11 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
     gam[(kind == VEL) | (kind == PRES)] = 1.0
     gam[kind == WALL] = 0.0
     width = min(wy, wz)
-    tau = tau_from_re(re, umax, width)
-    nu = (tau - 0.5) / 3.0
     lat = Lattice(f"heat_sink_{nx}x{ny}x{nz}", D3Q19, nx, ny, nz, flags.ravel(),
-                  gam.ravel(), bc.ravel(), tau=tau, gamma_model=gamma_model,
-                  thermal=True, kappa_f=nu / pr, k_ratio=k_ratio, q_flux=q_flux,
-                  T0=0.0, w_pin=w_pin, w_tmean=w_tmean)
+                  gam.ravel(), bc.ravel(), gamma_model=gamma_model,
+                  thermal=True, k_ratio=k_ratio, q_flux=q_flux,
+                  T0=0.0, w_pin=w_pin, w_tmean=w_tmean,
+                  re=re, u_ref=umax, l_ref=float(width), pr=pr)
     lat.meta.update(width=width, umax=umax, re=re, pr=pr, seed=seed)
     return lat
 

@@ -148,14 +148,17 @@ class Batch:
     """Thin owner of an lbm_batch (same names as the C-ABI)."""
 
     def __init__(self, storage: str = "fp32", check_every: int = 500, max_slots: int = 32,
-                 solo_tiles: int | None = None):
+                 solo_tiles: int | None = None, budget_bytes: int = 0):
         """solo_tiles: lattices with at least this many 256-node tiles run their
         own single-lattice graph beside the packed launch (0: pack every
-        lattice; None: the library's default, one wave of the packed launch)."""
+        lattice; None: the library's default, one wave of the packed launch).
+        budget_bytes: device memory the batch's contexts may hold together,
+        admitted or kept for a warm start (0: no limit); the library counts it."""
         self.lib = C.lib()
         self._b = ctypes.c_void_p()
         C.check(self.lib.lbm_batch_create(ctypes.byref(self._b), STORAGES[storage],
-                                          int(check_every), int(max_slots)), "lbm_batch_create")
+                                          int(check_every), int(max_slots), int(budget_bytes)),
+                "lbm_batch_create")
         if solo_tiles is not None:
             C.check(self.lib.lbm_batch_set_solo_tiles(self._b, int(solo_tiles)),
                     "lbm_batch_set_solo_tiles")
@@ -170,6 +173,25 @@ class Batch:
         C.check(self.lib.lbm_batch_admit(self._b, solver._ctx, ctypes.byref(o), ctypes.byref(slot)),
                 "lbm_batch_admit")
         return slot.value
+
+    def try_admit(self, solver: Solver, tol: float, max_steps: int, reset: bool):
+        """admit, or None when the context does not fit the memory budget now"""
+        o = C.lbm_solve_opts(float(tol), int(max_steps), 0, int(reset))
+        slot = ctypes.c_int()
+        code = self.lib.lbm_batch_admit(self._b, solver._ctx, ctypes.byref(o), ctypes.byref(slot))
+        if code == C.LBM_ERR_OOM:
+            return None
+        C.check(code, "lbm_batch_admit")
+        return slot.value
+
+    def release(self, solver: Solver):
+        C.check(self.lib.lbm_batch_release(self._b, solver._ctx), "lbm_batch_release")
+
+    def memory(self):
+        """(budget, bytes counted now)"""
+        b, h = ctypes.c_size_t(), ctypes.c_size_t()
+        C.check(self.lib.lbm_batch_memory(self._b, ctypes.byref(b), ctypes.byref(h)), "lbm_batch_memory")
+        return b.value, h.value
 
     def step(self) -> int:
         n = ctypes.c_int()
@@ -212,15 +234,15 @@ class Server:
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(free * 0.8)
-        self.budget = budget_bytes
-        self.used = 0
         self.tol, self.max_steps = tol, max_steps
         self.keep = keep_designs
         # about a million in-flight nodes (one 192x96x48 lattice plus small
         # ones) already keep every SM busy; admitting more only shares the GPU
         # among more requests and lengthens everyone's latency
         self.max_active_nodes = max_active_nodes
-        self.batch = Batch(storage, check_every, max_slots, solo_tiles)
+        # the library's batch counts every context it admitted until it is
+        # destroyed (running or kept for a warm start) against this budget
+        self.batch = Batch(storage, check_every, max_slots, solo_tiles, budget_bytes)
         self.max_slots = max_slots
         self.resident = OrderedDict()   # design id -> (solver, lattice, gamma, last sens, bytes)
         self.offloaded = OrderedDict()  # design id -> (lattice, gamma, last sens, host state)
@@ -229,6 +251,19 @@ class Server:
         self.n_restored = 0             # designs brought back from host memory
         self.active = {}                # ctx pointer value -> (request, result, design id)
         self.prep = LatticePrep()
+
+    @property
+    def budget(self) -> int:
+        return self.batch.memory()[0]
+
+    @property
+    def used(self) -> int:
+        """device bytes of the resident designs, as the library counts them"""
+        return self.batch.memory()[1]
+
+    def _trim_host(self):
+        while self.host_used > self.host_budget and self.offloaded:
+            self.host_used -= self.offloaded.popitem(last=False)[1][3].numel()
 
     def _evict_one(self) -> bool:
         """Free the least recently used idle design's device memory; a design
@@ -243,10 +278,8 @@ class Server:
                     self.offloaded[d] = (lat, gamma.cpu(), sens, state)
                     self.offloaded.move_to_end(d)
                     self.host_used += state.numel()
-                    while self.host_used > self.host_budget and self.offloaded:
-                        self.host_used -= self.offloaded.popitem(last=False)[1][3].numel()
-                s.close()
-                self.used -= nb
+                    self._trim_host()
+                s.close()  # lbm_destroy: the batch stops counting it
                 return True
         return False
 
@@ -259,7 +292,7 @@ class Server:
         return sum(int(np.prod(r.shape)) for (r, _, _) in self.active.values())
 
     def _make_room(self, nb: int) -> bool:
-        while self.used + nb > self.budget:
+        while self.budget and self.used + nb > self.budget:
             if not self._evict_one():
                 return False
         return True
@@ -289,6 +322,7 @@ class Server:
             if not self._make_room(nb):
                 self.offloaded[d] = (lat, gamma_h, sens, state)
                 self.host_used += state.numel()
+                self._trim_host()
                 return False
             s = Solver.from_lattice(lat, storage=self.storage, device=self.device)
             s.import_state(state)
@@ -296,7 +330,6 @@ class Server:
             gamma = opt_step_gamma(lat, gamma_h.to(self.device), sens)
             s.set_gamma(gamma)
             self.resident[d] = (s, lat, gamma, sens, nb)
-            self.used += nb
             warm = True
             self.prep.drop(req)
         else:
@@ -310,12 +343,9 @@ class Server:
                 # no state of the design is kept any more: replay its update cold
                 gamma = gamma.clone()
             if d in self.resident:
-                old = self.resident.pop(d)
-                old[0].close()
-                self.used -= old[4]
+                self.resident.pop(d)[0].close()
             self.offloaded.pop(d, None)
             self.resident[d] = (s, lat, gamma, None, nb)
-            self.used += nb
         self.batch.admit(s, self.tol, self.max_steps, reset=not warm)
         res.admitted = now
         res.warm = warm
@@ -386,9 +416,7 @@ class Server:
                 res.done = time.perf_counter() - t0
                 done += 1
                 if not self.keep or rep.status < 0:
-                    ent = self.resident.pop(d)
-                    ent[0].close()
-                    self.used -= ent[4]
+                    self.resident.pop(d)[0].close()
         return [results[r.rid] for r in requests]
 
     def close(self):

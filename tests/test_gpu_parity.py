@@ -185,8 +185,7 @@ def test_new_inputs_on_a_used_context_match_a_fresh_context():
         s.set_flags(torch.as_tensor(lat.flags))
         s.set_gamma(torch.as_tensor(lat.gamma, dtype=torch.float32))
         s.set_bc_values(torch.as_tensor(lat.bcval, dtype=torch.float32))
-        s.set_params(tau=lat.tau, rho0=lat.rho0, gamma_model=lat.gamma_model)
-        s.set_objective(lat.w_pin, lat.w_tmean)
+        s.set_lattice_params(lat)
         got = solve(s)
         fresh = Solver.from_lattice(lat, storage="fp32")
         ref = solve(fresh)

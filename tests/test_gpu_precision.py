@@ -1,5 +1,6 @@
-"""16-bit offset storage (FP16 / BF16 populations, FP16 adjoint, FP32
-arithmetic): error against the FP64 oracle per field after fixed steps."""
+"""16-bit offset storage (FP16 / BF16 flow populations; adjoint and
+temperature populations stay FP32; FP32 arithmetic): error against the FP64
+oracle per field after fixed steps."""
 import json
 import os
 

@@ -2,7 +2,8 @@
 Q = beta_max (1 - gamma)(1 - T) in the temperature collision (Eq. 69, 71)
 and the objective J_Q = -sum Q (Eq. 72).  Pinned to a closed form, to the
 tangent/transposition identities of the thermal step, and to central finite
-differences of the converged objective.  The CUDA solver refuses it."""
+differences of the converged objective.  (The CUDA path's parity with it is
+in test_gpu_heatgen.py.)"""
 import ctypes
 
 import numpy as np
@@ -84,9 +85,3 @@ def test_objective_is_minus_the_generated_heat(oracle_mod):
 def test_sensitivity_with_heat_generation_vs_finite_difference(oracle_mod):
     lat = _heat_sink_with_source()
     _fd_check(oracle_mod, lat, _sample_cells(lat, 5, 3))
-
-
-def test_cuda_solver_refuses_the_variant():
-    from paper_2501_02161_gb300.solver import Solver
-    with pytest.raises(NotImplementedError):
-        Solver.from_lattice(_heat_sink_with_source())

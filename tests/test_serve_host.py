@@ -56,22 +56,42 @@ class FakeSolver:
 
     def close(self):
         FakeSolver.live.pop(self._ctx.value, None)
+        for b in FakeBatch.instances:  # lbm_destroy releases it from its batch
+            b.held.pop(self._ctx.value, None)
 
 
 class FakeBatch:
     """Completes a context after a number of steps proportional to its nodes
-    (one step per 32^3 worth of nodes); records what ran together."""
+    (one step per 32^3 worth of nodes); records what ran together; counts
+    admitted contexts against the memory budget like the library's batch."""
     instances = []
 
-    def __init__(self, storage, check_every, max_slots, solo_tiles=None):
+    def __init__(self, storage, check_every, max_slots, solo_tiles=None, budget_bytes=0):
         self.active = {}
         self.log = []
         self.done = []
+        self.storage = storage
+        self.budget = budget_bytes
+        self.held = {}
         FakeBatch.instances.append(self)
 
-    def admit(self, solver, tol, max_steps, reset):
-        self.active[solver._ctx.value] = [solver, max(1, solver.N // 32768), reset]
+    def memory(self):
+        return self.budget, sum(self.held.values())
+
+    def try_admit(self, solver, tol, max_steps, reset):
+        k = solver._ctx.value
+        if k not in self.held:
+            fp = S.footprint(solver.lat, self.storage)
+            if self.budget and sum(self.held.values()) + fp > self.budget:
+                return None
+            self.held[k] = fp
+        self.active[k] = [solver, max(1, solver.N // 32768), reset]
         return 0
+
+    def admit(self, solver, tol, max_steps, reset):
+        slot = self.try_admit(solver, tol, max_steps, reset)
+        assert slot is not None, "over the memory budget"
+        return slot
 
     def step(self):
         self.log.append(sorted(self.active))
@@ -118,7 +138,7 @@ def test_lattice_prefetch_gives_the_same_lattices():
     for r in reqs:
         a, b = prep.get(r), S.lattice_for(r)
         assert np.array_equal(a.flags, b.flags) and np.array_equal(a.gamma, b.gamma)
-        assert np.array_equal(a.bcval, b.bcval) and a.tau == b.tau
+        assert np.array_equal(a.bcval, b.bcval) and a.re == b.re
     prep.close()
 
 
