@@ -66,7 +66,9 @@ def parse():
                         "streams; batchcmp: batched vs single-context throughput; levelset: the "
                         "level-set optimiser on the 2D pipe bend")
     p.add_argument("--iters", type=int, default=50, help="autograd / levelset modes: optimisation iterations")
-    p.add_argument("--nreq", type=int, default=16, help="served requests per stream (serve mode: 256)")
+    p.add_argument("--nreq", type=int, default=256, help="served requests of the as-specified stream")
+    p.add_argument("--nreq-stable", type=int, default=64,
+                   help="served requests of the stable-Re stream (0: skip it)")
     p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
@@ -178,33 +180,40 @@ def run_levelset(args):
 
 
 def run_serve(args, nreq=None, device="cuda:0"):
-    """Config-5 style serving: seeded sensitivity / optimisation-step requests
-    over 32^3 ... 192x96x48 lattices, half thermal, 20 % optimisation steps,
-    forward + adjoint to 1e-4 (20000-step cap per phase).  Two streams:
-    "as_specified" with Re ~ U[10, 500] (most requests diverge with BGK at
-    these inlet widths; they count as failed) and "stable_re" with
-    Re ~ U[10, 80] (the paper's 3D maximum was 80).
-    offline: all requests at t=0 through (a) the sequential plain-FP32 path,
-    (b) the batched FP32 server, (c) the batched server with FP16 flow storage.
-    online (stable stream): Poisson arrivals at 0.8 x the batched FP32 offline
-    request rate, through all three.  Latency = completion - arrival;
-    sens/s = completed requests / wall time."""
+    """Config-5 serving: seeded sensitivity / optimisation-step requests over
+    32^3 ... 192x96x48 lattices, half thermal, 20 % optimisation steps,
+    forward + adjoint to 1e-4 (20000-step cap per phase).
+    "as_specified": Re ~ U[10, 500], --nreq requests (256 by default), offline
+    (all at t=0) and online (Poisson arrivals at 0.8 x the batched FP32 offline
+    rate), each through (a) the sequential plain-FP32 path, (b) the batched
+    FP32 server, (c) the batched server with FP16 flow storage; with BGK at
+    these inlet widths most requests above Re ~ 80 diverge and count as
+    failed (by_shape / by_re break the failures down).
+    "stable_re": Re ~ U[10, 80] (the paper's 3D range), --nreq-stable
+    requests, offline, the same three paths.
+    "accuracy": for up to 8 completed sensitivity requests of the stable
+    stream, dJ/dgamma of the sequential FP32 and batched FP16 results against
+    a reference solve of the same request (FP64 storage, tolerance 1e-8).
+    Latency = completion - arrival; sens/s = completed requests / wall time."""
     import numpy as np
     import torch
 
     from paper_2501_02161_gb300 import build as B
-    from paper_2501_02161_gb300.serve import Server, make_requests, serve_sequential, summarize
+    from paper_2501_02161_gb300.serve import (Server, lattice_for, make_requests, serve_sequential,
+                                              summarize)
+    from paper_2501_02161_gb300.solver import Solver
 
     B.build()
     n = nreq or args.nreq
     tol, cap, K = 1e-4, 20000, 500
 
+    def rel(a, b):
+        return float(torch.linalg.norm(a.double() - b.double()) /
+                     torch.linalg.norm(b.double()).clamp_min(1e-30))
+
     def agree(res, ref):
-        errs = []
-        for a, b in zip(res, ref):
-            if a.status == 0 and b.status == 0 and a.sens is not None and b.sens is not None:
-                errs.append(float(torch.linalg.norm(a.sens - b.sens) /
-                                  torch.linalg.norm(b.sens).clamp_min(1e-30)))
+        errs = [rel(a.sens, b.sens) for a, b in zip(res, ref)
+                if a.status >= 0 and b.status >= 0 and a.sens is not None and b.sens is not None]
         return {"median": float(np.median(errs)) if errs else None,
                 "max": float(np.max(errs)) if errs else None, "n": len(errs)}
 
@@ -228,22 +237,54 @@ def run_serve(args, nreq=None, device="cuda:0"):
             srv = Server(storage, check_every=K, max_slots=32, tol=tol, max_steps=cap, device=device)
             res[f"batched_{storage}"] = srv.run(reqs, realtime=realtime)
             srv.close()
-        summ = {k: summarize(v) for k, v in res.items()}
+        summ = {k: summarize(v, requests=reqs) for k, v in res.items()}
         for k in ("batched_fp32", "batched_fp16"):
             summ[k]["dJdgamma_rel_l2_vs_sequential_fp32"] = agree(res[k], res["sequential_fp32"])
-        return summ
+        return summ, res
+
+    def accuracy(reqs, res, count=8):
+        seq, f16 = res["sequential_fp32"], res["batched_fp16"]
+        rows = []
+        for q, a, b in zip(reqs, seq, f16):
+            if len(rows) >= count:
+                break
+            if q.kind != "sens" or a.status != 0 or b.status != 0:
+                continue
+            lat = lattice_for(q)
+            s = Solver.from_lattice(lat, storage="fp64", device=device)
+            rf = s.forward(tol=1e-8, max_steps=400000, check_every=K, strict=False)
+            ra = s.adjoint(tol=1e-8, max_steps=400000, check_every=K, strict=False) if rf.status >= 0 else rf
+            if ra.status >= 0:
+                ref = s.sensitivity(dtype=torch.float64)
+                rows.append({"shape": list(q.shape), "re": round(q.re, 1), "thermal": q.thermal,
+                             "sequential_fp32": rel(a.sens.to(ref.device), ref),
+                             "batched_fp16": rel(b.sens.to(ref.device), ref)})
+            s.close()
+        col = lambda k: [r[k] for r in rows]
+        return {"reference": "same request, FP64 storage, forward + adjoint to 1e-8",
+                "n": len(rows),
+                "sequential_fp32": {"median": float(np.median(col("sequential_fp32"))) if rows else None,
+                                    "max": float(np.max(col("sequential_fp32"))) if rows else None},
+                "batched_fp16": {"median": float(np.median(col("batched_fp16"))) if rows else None,
+                                 "max": float(np.max(col("batched_fp16"))) if rows else None},
+                "requests": rows}
 
     out = {"requests_per_stream": n, "tol": tol, "max_steps_per_phase": cap, "check_every": K,
            "shapes": "32^3, 64^3, 96x48x24, 128x64x32, 192x96x48", "thermal_fraction": 0.5,
            "opt_step_fraction": 0.2}
     warm()
-    out["as_specified_re_10_500"] = {"offline": run_all(make_requests(n, seed=5, rate=None), False)}
-    stable = {"offline": run_all(make_requests(n, seed=5, rate=None, re_range=(10.0, 80.0)), False)}
-    off = stable["offline"]["batched_fp32"]
+    spec = {}
+    spec["offline"], _ = run_all(make_requests(n, seed=5, rate=None), False)
+    off = spec["offline"]["batched_fp32"]
     rate = 0.8 * n / max(off["wall_s"], 1e-9)
-    stable["online_rate_per_s"] = round(rate, 3)
-    stable["online"] = run_all(make_requests(n, seed=5, rate=rate, re_range=(10.0, 80.0)), True)
-    out["stable_re_10_80"] = stable
+    spec["online_rate_per_s"] = round(rate, 3)
+    spec["online"], _ = run_all(make_requests(n, seed=5, rate=rate), True)
+    out["as_specified_re_10_500"] = spec
+    ns = args.nreq_stable
+    if ns > 0:
+        reqs = make_requests(ns, seed=5, rate=None, re_range=(10.0, 80.0))
+        summ, res = run_all(reqs, False)
+        out["stable_re_10_80"] = {"requests": ns, "offline": summ, "accuracy": accuracy(reqs, res)}
     return out
 
 

@@ -34,12 +34,18 @@
  *             density, Eq. 8)
  *   bits 3-5  inward normal of an open boundary or heated wall:
  *             0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
- *   bit 6     HEAT: a WALL node that adds q_flux per step to the temperature
- *             population along its normal
+ *   bit 6     on a WALL node, HEAT: adds q_flux per step to the temperature
+ *             population along its normal; on a PRES node, temperature inlet:
+ *             the temperature is held at T_in (bc value 3) instead of the
+ *             outflow condition (a pressure-driven inlet, Eq. 70)
  *   bit 7     must be 0
  *
  * Boundary values, 4 numbers per node, read only at VEL / PRES nodes:
- *   VEL: (ux, uy, uz, T_in)       PRES: (rho_out, unused, unused, unused)
+ *   VEL: (ux, uy, uz, T_in)       PRES: (rho, unused, unused, T_in if bit 6)
+ *
+ * Faces of the lattice box: streaming wraps periodically across them, unless
+ * lbm_set_symmetry makes an axis reflect (symmetry planes half a node beyond
+ * both of its faces).
  *
  * Population order (for lbm_get_adjoint / state export):
  *   D2Q9  : 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+,+), 6 (-,+), 7 (-,-), 8 (+,-)
@@ -187,6 +193,17 @@ lbm_status lbm_set_physics(lbm_ctx* ctx, const lbm_physics* ph);
 /* Objective weights.  Non-finite weights, or w_qgen != 0 without the
  * thermal lattice, give LBM_ERR_ARG. */
 lbm_status lbm_set_objective(lbm_ctx* ctx, const lbm_objective* obj);
+
+/* Symmetry planes (the quarter-domain heat sink of Sec. 3.3): bit a of axes
+ * makes streaming along axis a reflect at both faces of the box instead of
+ * wrapping: a pull that leaves the box reads the image node in the plane half
+ * a node beyond the face, with that component of the population's direction
+ * reversed.  Streaming stays a permutation, so the adjoint (Eq. 61) is the
+ * same reflection.  A face that is not meant as a plane carries walls or open
+ * boundaries (whose pulls from outside the box are overwritten or never
+ * read).  Default 0 (all periodic).  Errors: LBM_ERR_ARG (bits above 2; bit 2
+ * for D2Q9). */
+lbm_status lbm_set_symmetry(lbm_ctx* ctx, int axes);
 
 /* Boundary values of one face of the lattice box (the per-node form is
  * lbm_set_bc_values).  face: the inward normal code of the face (0: x = 0,

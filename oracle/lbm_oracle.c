@@ -23,7 +23,9 @@
  *
  * Layout: array of structures, f[n*Q + i], node n = x + nx*(y + ny*z).
  * Node flags follow the documented byte layout (type in bits 0-2, inward
- * normal code in bits 3-5, HEAT in bit 6).
+ * normal code in bits 3-5, bit 6: a heated wall, or a fixed-density node that
+ * holds the temperature at T_in, i.e. a pressure-driven inlet).  Faces of the
+ * box are periodic seams or, per P->mirror, symmetry planes.
  *
  * Plain loops on purpose: no blocking, no fusion beyond the equations.  The
  * outer node loops carry an OpenMP pragma so the CPU baseline can use the
@@ -56,6 +58,12 @@ typedef struct {
      * added as w_k Q in the temperature collision; objective weight w_qgen
      * of J_Q = -sum_nonwall Q.  Both 0 switch the variant off. */
     double beta_max, w_qgen;
+    /* symmetry planes: bit a makes both faces of axis a mirrors half a node
+     * beyond the boundary layers instead of a periodic seam (a box cannot be
+     * periodic along an axis with a plane on one side; a face that is not
+     * meant as a plane carries walls or open boundaries, whose pulls from
+     * outside the box are overwritten or never read) */
+    int mirror;
 } orc_problem;
 
 typedef struct {
@@ -132,12 +140,39 @@ static void node_normal(uint8_t fl, int n[3]) {
 
 static long nnodes(const orc_problem* P) { return (long)P->nx * P->ny * P->nz; }
 
-static long neighbour(const orc_problem* P, long n, int dx, int dy, int dz) {
-    long x = n % P->nx, y = (n / P->nx) % P->ny, z = n / ((long)P->nx * P->ny);
-    x = ((x + dx) % P->nx + P->nx) % P->nx;
-    y = ((y + dy) % P->ny + P->ny) % P->ny;
-    z = ((z + dz) % P->nz + P->nz) % P->nz;
-    return x + (long)P->nx * (y + (long)P->ny * z);
+/* flat index (node * Q + population) that streaming reads for population i
+ * at node n: the node x + sgn e_i (sgn = -1: the forward pull of Eq. 37;
+ * sgn = +1: the adjoint's reverse pull of Eq. 61), wrapped periodically,
+ * except along an axis with symmetry planes: there the source is the image
+ * of that node in the plane (half a node beyond the face) and the population
+ * is e_i with that component reversed (specular reflection).  Streaming stays
+ * a permutation, and the reverse pull is its transpose. */
+static long stream_src(const orc_problem* P, const lattice* L, long n, int i, int sgn) {
+    const long dim[3] = {P->nx, P->ny, P->nz};
+    long c[3] = {n % P->nx, (n / P->nx) % P->ny, n / ((long)P->nx * P->ny)};
+    int e[3] = {L->e[i][0], L->e[i][1], L->e[i][2]};
+    for (int a = 0; a < 3; a++) {
+        long v = c[a] + sgn * e[a];
+        if (v < 0) {
+            if (P->mirror & (1 << a)) {
+                v = -1 - v;
+                e[a] = ORC_MUTATION == 11 ? e[a] : -e[a];
+            } else {
+                v += dim[a];
+            }
+        } else if (v >= dim[a]) {
+            if (P->mirror & (1 << a)) {
+                v = 2 * dim[a] - 1 - v;
+                e[a] = ORC_MUTATION == 11 ? e[a] : -e[a];
+            } else {
+                v -= dim[a];
+            }
+        }
+        c[a] = v;
+    }
+    int j = 0;
+    while (j < L->Q && !(L->e[j][0] == e[0] && L->e[j][1] == e[1] && L->e[j][2] == e[2])) j++;
+    return (c[0] + (long)P->nx * (c[1] + (long)P->ny * c[2])) * L->Q + j;
 }
 
 static double dot3(const double a[3], const double b[3]) {
@@ -368,8 +403,7 @@ void orc_flow_step(const orc_problem* P, const uint8_t* flags, const double* gam
     for (long n = 0; n < N; n++) {
         double fs[QMAX];
         for (int i = 0; i < Q; i++) {
-            long src = neighbour(P, n, -L.e[i][0], -L.e[i][1], -L.e[i][2]);
-            fs[i] = fc[src * Q + i];
+            fs[i] = fc[stream_src(P, &L, n, i, -1)];
         }
         bc_node(&L, P, flags[n], bcval + 4 * n, fs, fnew + n * Q);
     }
@@ -420,7 +454,7 @@ void orc_flow_tangent(const orc_problem* P, const uint8_t* flags, const double* 
     for (long n = 0; n < N; n++) {
         double ds[QMAX], B[QMAX][QMAX];
         for (int i = 0; i < Q; i++)
-            ds[i] = dc[neighbour(P, n, -L.e[i][0], -L.e[i][1], -L.e[i][2]) * Q + i];
+            ds[i] = dc[stream_src(P, &L, n, i, -1)];
         bc_jacobian(&L, P, flags[n], B);
         for (int i = 0; i < Q; i++) {
             double s = 0;
@@ -460,9 +494,7 @@ static void adjoint_stream(const lattice* L, const orc_problem* P, const double*
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; n++)
         for (int i = 0; i < Q; i++)
-            fss[n * Q + i] = (ORC_MUTATION == 4)
-                                 ? fs[neighbour(P, n, -L->e[i][0], -L->e[i][1], -L->e[i][2]) * Q + i]
-                                 : fs[neighbour(P, n, L->e[i][0], L->e[i][1], L->e[i][2]) * Q + i];
+            fss[n * Q + i] = fs[stream_src(P, L, n, i, ORC_MUTATION == 4 ? -1 : 1)];
 }
 
 static long count_type(const orc_problem* P, const uint8_t* flags, int t) {
@@ -633,7 +665,7 @@ int orc_cont_adjoint_step(const orc_problem* P, const uint8_t* flags, const doub
     for (long n = 0; n < N; n++) {
         double t[9];
         for (int i = 0; i < Q; i++)
-            t[i] = c[neighbour(P, n, L.e[i][0], L.e[i][1], L.e[i][2]) * Q + i]; /* reverse stream */
+            t[i] = c[stream_src(P, &L, n, i, 1)]; /* reverse stream */
         cont_bc_node(&L, flags[n], s_in, t);
         for (int i = 0; i < Q; i++) fs_new[n * Q + i] = t[i];
     }
@@ -734,7 +766,8 @@ static void thermal_bc_node(const lattice* LG, const orc_problem* P, uint8_t fl,
     double K = 0;
     for (int k = 0; k < LG->Q; k++)
         if (k != kn) K += gs[k];
-    if (t == T_VEL) {
+    if (t == T_VEL || (fl & 0x40)) { /* inlet: T held at T_in (a fixed-density node with
+                                         bit 6 is a pressure-driven inlet, Eq. 70) */
         out[kn] = bcv[3] - K;
     } else {
         double e[3];
@@ -770,7 +803,7 @@ void orc_thermal_step(const orc_problem* P, const uint8_t* flags, const double* 
     for (long n = 0; n < N; n++) {
         double gs[7], u[3];
         for (int k = 0; k < 7; k++)
-            gs[k] = gc[neighbour(P, n, -LG.e[k][0], -LG.e[k][1], -LG.e[k][2]) * 7 + k];
+            gs[k] = gc[stream_src(P, &LG, n, k, -1)];
         flow_u(&LF, P, f + n * LF.Q, u);
         thermal_bc_node(&LG, P, flags[n], gamma[n], u, bcval + 4 * n, gs, gnew + n * 7);
     }
@@ -859,7 +892,7 @@ static void thermal_bc_jacobians(const lattice* LF, const lattice* LG, const orc
     int kn = unknown_dir(LG, n);
     for (int k = 0; k < 7; k++)
         if (k != kn) Bg[k][k] = 1.0;
-    if (t == T_VEL) {
+    if (t == T_VEL || (fl & 0x40)) {
         for (int l = 0; l < 7; l++)
             if (l != kn) Bg[kn][l] = -1.0;
         return;
@@ -895,7 +928,7 @@ static void thermal_poststream(const lattice* LF, const lattice* LG, const orc_p
     }
     for (long n = 0; n < N; n++)
         for (int k = 0; k < 7; k++)
-            gs_all[n * 7 + k] = gc[neighbour(P, n, -LG->e[k][0], -LG->e[k][1], -LG->e[k][2]) * 7 + k];
+            gs_all[n * 7 + k] = gc[stream_src(P, LG, n, k, -1)];
     free(gc);
 }
 
@@ -926,7 +959,7 @@ void orc_thermal_tangent(const orc_problem* P, const uint8_t* flags, const doubl
     for (long n = 0; n < N; n++) {
         double ds[7], u[3], Bg[7][7], Bf[7][QMAX], Bgam[7];
         for (int k = 0; k < 7; k++)
-            ds[k] = dc[neighbour(P, n, -LG.e[k][0], -LG.e[k][1], -LG.e[k][2]) * 7 + k];
+            ds[k] = dc[stream_src(P, &LG, n, k, -1)];
         flow_u(&LF, P, f + n * Q, u);
         thermal_bc_jacobians(&LF, &LG, P, flags[n], gamma[n], u, gs_all + n * 7, Bg, Bf, Bgam);
         for (int k = 0; k < 7; k++) {
@@ -992,7 +1025,7 @@ void orc_thermal_adjoint_step(const orc_problem* P, const uint8_t* flags, const 
     for (long n = 0; n < N; n++) {
         double gss[7], u[3], Cg[7][7], Cf[7][QMAX], Cgam[7];
         for (int k = 0; k < 7; k++)
-            gss[k] = gst[neighbour(P, n, LG.e[k][0], LG.e[k][1], LG.e[k][2]) * 7 + k];
+            gss[k] = gst[stream_src(P, &LG, n, k, 1)];
         flow_u(&LF, P, f + n * Q, u);
         thermal_collision_jacobians(&LF, &LG, P, flags[n], gamma[n], u, g + n * 7, Cg, Cf, Cgam);
         /* dJ_Q/dg_l = w_qgen beta_max (1 - gamma) at non-wall nodes (Eq. 72) */
@@ -1055,7 +1088,7 @@ void orc_thermal_coupling(const orc_problem* P, const uint8_t* flags, const doub
     for (long n = 0; n < N; n++) {
         double gss[7], u[3], Cg[7][7], Cf[7][QMAX], Cgam[7];
         for (int k = 0; k < 7; k++)
-            gss[k] = gst[neighbour(P, n, LG.e[k][0], LG.e[k][1], LG.e[k][2]) * 7 + k];
+            gss[k] = gst[stream_src(P, &LG, n, k, 1)];
         flow_u(&LF, P, f + n * Q, u);
         thermal_collision_jacobians(&LF, &LG, P, flags[n], gamma[n], u, g + n * 7, Cg, Cf, Cgam);
         for (int i = 0; i < Q; i++) {

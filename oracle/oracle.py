@@ -43,7 +43,7 @@ class Problem(ctypes.Structure):
                 ("kappa_f", ctypes.c_double), ("k_ratio", ctypes.c_double),
                 ("q_flux", ctypes.c_double), ("w_pin", ctypes.c_double),
                 ("w_tmean", ctypes.c_double), ("beta_max", ctypes.c_double),
-                ("w_qgen", ctypes.c_double)]
+                ("w_qgen", ctypes.c_double), ("mirror", ctypes.c_int)]
 
 
 _lib = None
@@ -130,10 +130,11 @@ def lattice_tables(which: int):
 
 def make_problem(stencil, nx, ny, nz, tau, rho0=1.0, gamma_model=0, thermal=False,
                  kappa_f=0.0, k_ratio=1.0, q_flux=0.0, w_pin=1.0, w_tmean=0.0,
-                 beta_max=0.0, w_qgen=0.0) -> Problem:
+                 beta_max=0.0, w_qgen=0.0, mirror=0) -> Problem:
     return Problem(int(stencil), int(nx), int(ny), int(nz), float(tau), float(rho0),
                    int(gamma_model), int(bool(thermal)), float(kappa_f), float(k_ratio),
-                   float(q_flux), float(w_pin), float(w_tmean), float(beta_max), float(w_qgen))
+                   float(q_flux), float(w_pin), float(w_tmean), float(beta_max), float(w_qgen),
+                   int(mirror))
 
 
 def rel_change(a: float, b: float) -> float:
@@ -166,7 +167,8 @@ class Oracle:
         tau, kappa_f = relaxation_of(lat)
         self.P = make_problem(lat.stencil, lat.nx, lat.ny, lat.nz, tau, lat.rho0,
                               lat.gamma_model, lat.thermal, kappa_f, lat.k_ratio,
-                              lat.q_flux, lat.w_pin, lat.w_tmean, lat.beta_max, lat.w_qgen)
+                              lat.q_flux, lat.w_pin, lat.w_tmean, lat.beta_max, lat.w_qgen,
+                              lat.mirror)
         self.Q = 9 if lat.stencil == 0 else 19
         self.N = lat.n
         self.flags = np.ascontiguousarray(lat.flags, np.uint8)

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lbm_physics_to_params": (_I, [ctypes.POINTER(lbm_physics), ctypes.POINTER(lbm_params)]),
     "lbm_set_physics": (_I, [_VP, ctypes.POINTER(lbm_physics)]),
     "lbm_set_bc": (_I, [_VP, _I, _I, _VP, _SZ, _I, _I]),
+    "lbm_set_symmetry": (_I, [_VP, _I]),
     "lbm_forward": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_adjoint": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_solve_phase": (_I, [_VP, _I, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),

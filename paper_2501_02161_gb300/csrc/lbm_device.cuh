@@ -196,6 +196,7 @@ struct FlowArgs {
     R ascale;                        // adjoint storage scale: 1 in every storage mode
                                      // (the adjoint is stored at full precision)
     int model;                       // 0 EQ12, 1 LINEAR
+    int mirror;                      // bit a: axis a has symmetry planes beyond both faces
 };
 
 template <typename T, typename TA, typename R>
@@ -220,6 +221,7 @@ struct ThermArgs {
     R ascale;
     R beta;                          // beta_max: heat source Q = beta (1 - gamma)(1 - T) (Eq. 69)
     R src_q;                         // w_qgen beta_max: -dJ_Q/dg_l = -src_q (1 - gamma)
+    int mirror;                      // bit a: axis a has symmetry planes beyond both faces
 };
 
 // ---------------------------------------------------------------------------
@@ -266,6 +268,45 @@ __host__ __device__ __forceinline__ int nbr_offset(const Nbr& o, int i, int s) {
     const int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
     return (dx < 0 ? o.xm : (dx > 0 ? o.xp : 0)) + (dy < 0 ? o.ym : (dy > 0 ? o.yp : 0)) +
            (dz < 0 ? o.zm : (dz > 0 ? o.zp : 0));
+}
+
+// Symmetry planes.  Along an axis with planes (bit a of `mirror`) the faces
+// are not a periodic seam: a pull x + s e_i that leaves the box reads the
+// image of that node in the plane (half a node beyond the face) and the
+// population with that component of e_i reversed.  Only nodes on such a face
+// take this path.
+__host__ __device__ __forceinline__ bool on_mirror_face(const Cell& c, int nx, int ny, int nz, int mirror) {
+    return ((mirror & 1) && (c.x == 0 || c.x == nx - 1)) || ((mirror & 2) && (c.y == 0 || c.y == ny - 1)) ||
+           ((mirror & 4) && (c.z == 0 || c.z == nz - 1));
+}
+
+__host__ __device__ __forceinline__ int reflect_coord(int v, int n, bool plane, bool& flipped) {
+    if (v < 0) {
+        if (plane) { flipped = true; return -1 - v; }
+        return v + n;
+    }
+    if (v >= n) {
+        if (plane) { flipped = true; return 2 * n - 1 - v; }
+        return v - n;
+    }
+    return v;
+}
+
+// element index (plane * np + node) of the pull x + s e_i at a node on a
+// symmetry-plane face
+template <class L>
+__host__ __device__ __forceinline__ long long mirror_src(const Cell& c, int nx, int ny, int nz, long long np,
+                                                         int mirror, int i, int s) {
+    bool f0 = false, f1 = false, f2 = false;
+    const int x = reflect_coord(c.x + s * L::cx(i), nx, mirror & 1, f0);
+    const int y = reflect_coord(c.y + s * L::cy(i), ny, mirror & 2, f1);
+    const int z = reflect_coord(c.z + s * L::cz(i), nz, mirror & 4, f2);
+    const int e0 = f0 ? -L::cx(i) : L::cx(i), e1 = f1 ? -L::cy(i) : L::cy(i), e2 = f2 ? -L::cz(i) : L::cz(i);
+    int j = i;
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k)
+        if (L::cx(k) == e0 && L::cy(k) == e1 && L::cz(k) == e2) j = k;
+    return (long long)j * np + x + (long long)nx * (y + (long long)ny * z);
 }
 
 // Programmatic dependent launch (sm_90+): a step kernel lets the next step's
@@ -417,19 +458,33 @@ __device__ __forceinline__ void bounce(R (&f)[L::Q]) {
     }
 }
 
-// pull the post-collision populations of the upstream neighbours and apply B
+// the boundary operator B at a node, on its post-stream populations
 template <class L, typename T, typename TA, typename R>
-__device__ __forceinline__ int pull_forward(const FlowArgs<T, TA, R>& a, const Cell& c, R (&f)[L::Q]) {
-    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
-    const T* __restrict__ p = a.fin + c.n;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i, p += a.np) f[i] = Pop<T>::ld(p, nbr_offset<L>(o, i, -1), R(0));
-    const int fl = a.flags[c.n];
+__device__ __forceinline__ void apply_boundary(const FlowArgs<T, TA, R>& a, long long n, int fl, R (&f)[L::Q]) {
     const int type = fl & 7;
     if (type == WALL)
         bounce<L>(f);
     else if (type >= VEL)
-        zou_he<L>(f, type, (fl >> 3) & 7, a.bc + 4 * c.n, a.rho0);
+        zou_he<L>(f, type, (fl >> 3) & 7, a.bc + 4 * n, a.rho0);
+}
+
+// pull the post-collision populations of the upstream neighbours and apply B
+// (MIRROR: the lattice may have symmetry planes; without it that path is
+// compiled out)
+template <class L, bool MIRROR, typename T, typename TA, typename R>
+__device__ __forceinline__ int pull_forward(const FlowArgs<T, TA, R>& a, const Cell& c, R (&f)[L::Q]) {
+    if (MIRROR && a.mirror && on_mirror_face(c, a.nx, a.ny, a.nz, a.mirror)) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            f[i] = Pop<T>::ld(a.fin, mirror_src<L>(c, a.nx, a.ny, a.nz, a.np, a.mirror, i, -1), R(0));
+    } else {
+        const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+        const T* __restrict__ p = a.fin + c.n;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i, p += a.np) f[i] = Pop<T>::ld(p, nbr_offset<L>(o, i, -1), R(0));
+    }
+    const int fl = a.flags[c.n];
+    apply_boundary<L>(a, c.n, fl, f);
     return fl;
 }
 
@@ -455,26 +510,27 @@ __device__ __forceinline__ void moments(const R (&f)[L::Q], R rho0, R& rho, R& u
 // ---------------------------------------------------------------------------
 // forward kernels
 // ---------------------------------------------------------------------------
+// moments and BGK collision with the design coupling of one node's
+// post-boundary populations (in place); the reducing variant also writes the
+// node's fields and its residual / objective terms.  g is the node's gamma.
 template <class L, typename T, typename TA, typename R, bool REDUCE>
-__device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
-    R f[L::Q];
-    const int fl = pull_forward<L>(a, c, f);
+__device__ __forceinline__ void flow_collide(const FlowArgs<T, TA, R>& a, long long n, int fl, R g,
+                                             R (&f)[L::Q], double (&acc)[2]) {
     const int type = fl & 7;
     R drho, u0, u1, u2;
     moments<L>(f, a.rho0, drho, u0, u1, u2);
     using X = Ex<R>;
     if (REDUCE) {  // the fields and the frozen velocity of this post-boundary state
-        a.out0[c.n] = X::add(a.rho0, drho);
-        a.out1[c.n] = u0;
-        a.out1[a.np + c.n] = u1;
-        a.out1[2 * a.np + c.n] = u2;
+        a.out0[n] = X::add(a.rho0, drho);
+        a.out1[n] = u0;
+        a.out1[a.np + n] = u1;
+        a.out1[2 * a.np + n] = u2;
     }
     if (type != WALL) {
         if (REDUCE) {
             acc[0] = (double)sqrt(X::fma(u2, u2, X::fma(u1, u1, X::mul(u0, u0))));
             if (type == VEL) acc[1] = (double)X::add(a.rho0, drho);
         }
-        const R g = a.gamma[c.n];
         R a0, a1, a2, amp;
         if (a.model == 0) {
             a0 = X::mul(g, u0); a1 = X::mul(g, u1); a2 = X::mul(g, u2); amp = R(1);
@@ -502,6 +558,14 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
             f[j] = X::fma(om1, f[j], X::sub(even, odd));
         }
     }
+}
+
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool MIRROR = true>
+__device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
+    R f[L::Q];
+    const int fl = pull_forward<L, MIRROR>(a, c, f);
+    const R g = (fl & 7) != WALL ? a.gamma[c.n] : R(0);
+    flow_collide<L, T, TA, R, REDUCE>(a, c.n, fl, g, f, acc);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
         Pop<T>::st(a.fout, (size_t)i * a.np + c.n, f[i], R(0));
@@ -516,14 +580,100 @@ struct FwdMinBlocks {
     static constexpr int value = L::Q != 19 ? 1 : (sizeof(T) == 2 ? 6 : (sizeof(T) == 4 ? 5 : 1));
 };
 
-template <class L, typename T, typename TA, typename R, bool REDUCE>
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool MIRROR>
 __global__ void __launch_bounds__(256, (FwdMinBlocks<L, T>::value)) k_flow_step(FlowArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[2] = {0.0, 0.0};
-    if (c.active) flow_step_node<L, T, TA, R, REDUCE>(a, c, acc);
+    if (c.active) flow_step_node<L, T, TA, R, REDUCE, MIRROR>(a, c, acc);
     if (REDUCE) block_partials<2>(acc, a.partials, grid_block_id());
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit storage, two x-adjacent nodes per thread.  The populations of a node
+// pair (x0, x0 + 1), x0 even, sit in one aligned 32-bit word of each plane, so
+// a pull is one 32-bit load per direction when e_x = 0; when e_x = +1 (-1) the
+// pair pulled is (x0 - 1, x0) ((x0 + 1, x0 + 2)): the two aligned words around
+// it are loaded and one byte permute takes out the middle.  Each node then
+// runs the same boundary and collision code as the one-node kernels (so its
+// populations are bit-identical to theirs) and the results are stored as one
+// packed word per plane (one round-to-nearest-even pair conversion).  Needs an
+// even nx (every pair starts on an even node index); the reducing step keeps
+// the one-node kernel, so the per-block sums are those of every other path.
+// ---------------------------------------------------------------------------
+template <typename T> struct Pair16;
+template <> struct Pair16<__half> {
+    __device__ __forceinline__ static void unpack(uint32_t w, float& lo, float& hi) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        lo = v.x;
+        hi = v.y;
+    }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+};
+template <> struct Pair16<__nv_bfloat16> {
+    __device__ __forceinline__ static void unpack(uint32_t w, float& lo, float& hi) {
+        lo = __uint_as_float(w << 16);          // a bf16 is the high half of an f32
+        hi = __uint_as_float(w & 0xffff0000u);
+    }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+};
+
+template <class L, typename T>
+struct PairMinBlocks {
+    static constexpr int value = 3;
+};
+
+template <class L, typename T, typename TA, typename R>
+__global__ void __launch_bounds__(256, (PairMinBlocks<L, T>::value)) k_flow_step_pair(FlowArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    Cell c;
+    c.x = 2 * px;
+    c.y = blockIdx.y * blockDim.y + threadIdx.y;
+    c.z = blockIdx.z;
+    if (c.x >= a.nx || c.y >= a.ny) return;  // no block-wide step follows
+    c.n = c.x + (long long)a.nx * (c.y + (long long)a.ny * c.z);
+    c.active = true;
+    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+    const int xm2 = c.x == 0 ? a.nx - 2 : -2;           // the pair to the left, wrapped
+    const int xp2 = c.x + 2 == a.nx ? 2 - a.nx : 2;     // the pair to the right, wrapped
+    const uint32_t* __restrict__ p = reinterpret_cast<const uint32_t*>(a.fin + c.n);
+    const long long pstride = a.np >> 1;                // words per plane
+    uint32_t w[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i, p += pstride) {
+        const int dy = -L::cy(i), dz = -L::cz(i);
+        const int oyz = (dy < 0 ? o.ym : (dy > 0 ? o.yp : 0)) + (dz < 0 ? o.zm : (dz > 0 ? o.zp : 0));
+        const uint32_t mid = __ldg(p + (oyz >> 1));
+        if (L::cx(i) > 0) {
+            w[i] = __byte_perm(__ldg(p + ((oyz + xm2) >> 1)), mid, 0x5432);
+        } else if (L::cx(i) < 0) {
+            w[i] = __byte_perm(mid, __ldg(p + ((oyz + xp2) >> 1)), 0x5432);
+        } else {
+            w[i] = mid;
+        }
+    }
+    const uchar2 fl2 = *reinterpret_cast<const uchar2*>(a.flags + c.n);
+    const float2 g2 = *reinterpret_cast<const float2*>(a.gamma + c.n);
+    R fa[L::Q], fb[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Pair16<T>::unpack(w[i], fa[i], fb[i]);
+    double acc[2];
+    apply_boundary<L>(a, c.n, fl2.x, fa);
+    flow_collide<L, T, TA, R, false>(a, c.n, fl2.x, (fl2.x & 7) != WALL ? g2.x : R(0), fa, acc);
+    apply_boundary<L>(a, c.n + 1, fl2.y, fb);
+    flow_collide<L, T, TA, R, false>(a, c.n + 1, fl2.y, (fl2.y & 7) != WALL ? g2.y : R(0), fb, acc);
+    uint32_t* __restrict__ q = reinterpret_cast<uint32_t*>(a.fout + c.n);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) q[(size_t)i * pstride] = Pair16<T>::pack(fa[i], fb[i]);
 }
 
 // f = f^eq(rho0, 0) = w rho0, i.e. h = 0 (collision leaves it unchanged); f* = 0
@@ -577,8 +727,14 @@ struct AdjMoments {
     }
 };
 
-template <class L, typename T, typename TA, typename R>
+template <class L, bool MIRROR, typename T, typename TA, typename R>
 __device__ __forceinline__ void pull_adjoint(const FlowArgs<T, TA, R>& a, const Cell& c, R (&s)[L::Q]) {
+    if (MIRROR && a.mirror && on_mirror_face(c, a.nx, a.ny, a.nz, a.mirror)) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            s[i] = Pop<TA>::ld(a.ain, mirror_src<L>(c, a.nx, a.ny, a.nz, a.np, a.mirror, i, +1), R(0)) * a.ascale;
+        return;
+    }
     const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
     const TA* __restrict__ p = a.ain + c.n;
 #pragma unroll
@@ -597,10 +753,11 @@ struct AdjMinBlocks {
 
 // THERMAL: the coupling field is present; CPL_RT: decide at run time from
 // whether a coupling field is given (one code path for mixed batches)
-template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL, bool CPL_RT = false>
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL, bool CPL_RT = false,
+          bool MIRROR = true>
 __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
     R s[L::Q];
-    pull_adjoint<L>(a, c, s);
+    pull_adjoint<L, MIRROR>(a, c, s);
     const int fl = a.flags[c.n];
     const int type = fl & 7;
     if (type == WALL) {
@@ -659,19 +816,19 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
     }
 }
 
-template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL>
+template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL, bool MIRROR>
 __global__ void __launch_bounds__(256, (AdjMinBlocks<L, R, REDUCE, THERMAL>::value))
     k_flow_adjoint(FlowArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
-    if (c.active) flow_adjoint_node<L, T, TA, R, REDUCE, THERMAL>(a, c, acc);
+    if (c.active) flow_adjoint_node<L, T, TA, R, REDUCE, THERMAL, false, MIRROR>(a, c, acc);
     if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
 }
 
 // J'(x) = -(1/tau) sum_i f*_S,i d f^eq_i / d gamma (Eq. 66), + thermal part
-template <class L, typename T, typename TA, typename R, bool THERMAL>
+template <class L, typename T, typename TA, typename R, bool THERMAL, bool MIRROR>
 __global__ void __launch_bounds__(256) k_flow_sens(FlowArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     if (!c.active) return;
@@ -681,7 +838,7 @@ __global__ void __launch_bounds__(256) k_flow_sens(FlowArgs<T, TA, R> a) {
         return;
     }
     R s[L::Q];
-    pull_adjoint<L>(a, c, s);
+    pull_adjoint<L, MIRROR>(a, c, s);
     const R g = a.gamma[c.n];
     const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
     AdjMoments<L, R> m;
@@ -738,8 +895,8 @@ __device__ __forceinline__ void thermal_bc(R (&g)[7], int fl, const R* __restric
     for (int k = 0; k < 7; ++k)
         if (k != kn) K = X::add(K, g[k]);
     R val;
-    if (type == VEL) {
-        val = X::sub(bc[3], K);
+    if (type == VEL || (fl & HEAT_BIT)) {  // inlet: T held at T_in (bit 6 on a PRES node:
+        val = X::sub(bc[3], K);           // a pressure-driven inlet, Eq. 70)
     } else {
         R en = 0;
 #pragma unroll
@@ -753,14 +910,21 @@ __device__ __forceinline__ void thermal_bc(R (&g)[7], int fl, const R* __restric
         if (k == kn) g[k] = val;
 }
 
-template <typename T, typename TA, typename R>
+template <bool MIRROR, typename T, typename TA, typename R>
 __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const Cell& c, R (&g)[7],
                                             R& gam, R& u0, R& u1, R& u2) {
-    const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
-    const T* __restrict__ p = a.gin + c.n;
+    if (MIRROR && a.mirror && on_mirror_face(c, a.nx, a.ny, a.nz, a.mirror)) {
 #pragma unroll
-    for (int k = 0; k < 7; ++k, p += a.np)
-        g[k] = Pop<T>::ld(p, nbr_offset<D3Q7>(o, k, -1), R(D3Q7::w(k)) * a.T0);
+        for (int k = 0; k < 7; ++k)
+            g[k] = Pop<T>::ld(a.gin, mirror_src<D3Q7>(c, a.nx, a.ny, a.nz, a.np, a.mirror, k, -1),
+                              R(D3Q7::w(k)) * a.T0);
+    } else {
+        const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+        const T* __restrict__ p = a.gin + c.n;
+#pragma unroll
+        for (int k = 0; k < 7; ++k, p += a.np)
+            g[k] = Pop<T>::ld(p, nbr_offset<D3Q7>(o, k, -1), R(D3Q7::w(k)) * a.T0);
+    }
     const int fl = a.flags[c.n];
     gam = a.gamma[c.n];
     u0 = a.u[c.n];
@@ -773,10 +937,10 @@ __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const 
 // collision with the heat source w_k Q, Q = beta_max (1 - gamma)(1 - T)
 // (Eq. 69, 71); the reducing step also sums T (residual, mean-T objective)
 // and Q (heat-generation objective, Eq. 72) over non-wall nodes
-template <typename T, typename TA, typename R, bool REDUCE>
+template <typename T, typename TA, typename R, bool REDUCE, bool MIRROR = true>
 __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
     R g[7], gam, u0, u1, u2;
-    const int fl = thermal_pull(a, c, g, gam, u0, u1, u2);
+    const int fl = thermal_pull<MIRROR>(a, c, g, gam, u0, u1, u2);
     using X = Ex<R>;
     R tem = 0;
 #pragma unroll
@@ -805,13 +969,13 @@ __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, 
         Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);
 }
 
-template <typename T, typename TA, typename R, bool REDUCE>
+template <typename T, typename TA, typename R, bool REDUCE, bool MIRROR>
 __global__ void __launch_bounds__(256) k_thermal_step(ThermArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[2] = {0.0, 0.0};
-    if (c.active) thermal_step_node<T, TA, R, REDUCE>(a, c, acc);
+    if (c.active) thermal_step_node<T, TA, R, REDUCE, MIRROR>(a, c, acc);
     if (REDUCE) block_partials<2>(acc, a.partials, grid_block_id());
 }
 
@@ -857,18 +1021,25 @@ __device__ __forceinline__ void thermal_adjoint_collide(R (&s)[7], R gam, R u0, 
     for (int k = 0; k < 7; ++k) s[k] = X::fma(om1, s[k], base);
 }
 
-template <typename T, typename TA, typename R>
+template <bool MIRROR, typename T, typename TA, typename R>
 __device__ __forceinline__ void thermal_pull_adjoint(const ThermArgs<T, TA, R>& a, const Cell& c, R (&s)[7]) {
+    if (MIRROR && a.mirror && on_mirror_face(c, a.nx, a.ny, a.nz, a.mirror)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            s[k] = Pop<TA>::ld(a.ain, mirror_src<D3Q7>(c, a.nx, a.ny, a.nz, a.np, a.mirror, k, +1), R(0)) *
+                   a.ascale;
+        return;
+    }
     const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
     const TA* __restrict__ p = a.ain + c.n;
 #pragma unroll
     for (int k = 0; k < 7; ++k, p += a.np) s[k] = Pop<TA>::ld(p, nbr_offset<D3Q7>(o, k, +1), R(0)) * a.ascale;
 }
 
-template <typename T, typename TA, typename R, bool REDUCE>
+template <typename T, typename TA, typename R, bool REDUCE, bool MIRROR = true>
 __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
     R s[7];
-    thermal_pull_adjoint(a, c, s);
+    thermal_pull_adjoint<MIRROR>(a, c, s);
     const int fl = a.flags[c.n];
     const int type = fl & 7;
     if (type == WALL) {
@@ -890,7 +1061,7 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
                     en = ecomp<R>(k, u0, u1, u2);
                 }
             R coef;
-            if (type == VEL) {
+            if (type == VEL || (fl & HEAT_BIT)) {
                 coef = R(-1);
             } else {
                 const R wa = Ex<R>::mul(R(0.125), Ex<R>::fma(Ex<R>::mul(R(4), gam), en, R(1)));
@@ -912,13 +1083,13 @@ __device__ __forceinline__ void thermal_adjoint_node(const ThermArgs<T, TA, R>& 
     }
 }
 
-template <typename T, typename TA, typename R, bool REDUCE>
+template <typename T, typename TA, typename R, bool REDUCE, bool MIRROR>
 __global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const Cell c = this_cell(a.nx, a.ny);
     double acc[1] = {0.0};
-    if (c.active) thermal_adjoint_node<T, TA, R, REDUCE>(a, c, acc);
+    if (c.active) thermal_adjoint_node<T, TA, R, REDUCE, MIRROR>(a, c, acc);
     if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
 }
 
@@ -930,7 +1101,7 @@ __global__ void __launch_bounds__(256) k_thermal_adjoint(ThermArgs<T, TA, R> a) 
 // The outlet terms linearise the boundary operator at the post-stream state of
 // the stored temperature iterate (K = sum of its known post-stream
 // populations), the same point as the collision terms.
-template <typename T, typename TA, typename R>
+template <typename T, typename TA, typename R, bool MIRROR>
 __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a) {
     const Cell c = this_cell(a.nx, a.ny);
     if (!c.active) return;
@@ -939,7 +1110,7 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
     R v0 = 0, v1 = 0, v2 = 0, sT = 0;
     if (type != WALL) {
         R s[7];
-        thermal_pull_adjoint(a, c, s);
+        thermal_pull_adjoint<MIRROR>(a, c, s);
         const R gam = a.gamma[c.n];
         const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
         R gp[7], tem = 0;
@@ -971,7 +1142,7 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
         // direct part of J_Q = -w_qgen sum beta_max (1 - gamma)(1 - T)
         const R omT = R(1) - tem;
         sT = -s1 + a.beta * omT * W + a.src_q * omT;
-        if (type == PRES) {
+        if (type == PRES && !(fl & HEAT_BIT)) {  // outflow node (not a temperature inlet)
             const int kn = ((fl >> 3) & 7) + 1;
             R en = 0;
 #pragma unroll
@@ -980,11 +1151,14 @@ __global__ void __launch_bounds__(256) k_thermal_coupling(ThermArgs<T, TA, R> a)
             const R wa = R(0.125) * (R(1) + R(4) * gam * en);
             R K = 0;
             const Nbr o = neighbours(c, a.nx, a.ny, a.nz);
+            const bool mf = MIRROR && a.mirror && on_mirror_face(c, a.nx, a.ny, a.nz, a.mirror);
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
                 if (k == kn) continue;
-                K += Pop<T>::ld(a.gin + (long long)k * a.np + c.n, nbr_offset<D3Q7>(o, k, -1),
-                                R(D3Q7::w(k)) * a.T0);
+                K += mf ? Pop<T>::ld(a.gin, mirror_src<D3Q7>(c, a.nx, a.ny, a.nz, a.np, a.mirror, k, -1),
+                                     R(D3Q7::w(k)) * a.T0)
+                        : Pop<T>::ld(a.gin + (long long)k * a.np + c.n, nbr_offset<D3Q7>(o, k, -1),
+                                     R(D3Q7::w(k)) * a.T0);
             }
             const R dgda = R(0.125) * K / ((R(1) - wa) * (R(1) - wa));
             const R ckn = a.gcn[c.n];

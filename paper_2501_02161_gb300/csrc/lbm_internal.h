@@ -35,6 +35,7 @@ struct FlowLaunch {
     long long np;
     double omega, rho0, src_in, ascale;
     int model;
+    int mirror;
 };
 
 struct ThermLaunch {
@@ -54,6 +55,7 @@ struct ThermLaunch {
     int nx, ny, nz;
     long long np;
     double rho0, kappa_f, k_ratio, q, T0, src_T, ascale, beta, src_q;
+    int mirror;
 };
 
 enum FlowOp {

@@ -3,8 +3,7 @@
 #include <algorithm>
 #include <cstring>
 
-#include "lbm_device.cuh"
-#include "lbm_internal.h"
+#include "lbm_dispatch.cuh"
 
 namespace lbm {
 
@@ -22,143 +21,6 @@ Geom make_geom(int nx, int ny, int nz) {
 
 namespace {
 
-template <typename T> struct Types;
-// storage -> (population type, adjoint type, compute type)
-template <int S> struct StorageTypes;
-// T: flow populations, TG: temperature populations, TA: adjoint populations.
-// The 16-bit modes narrow only the flow populations: the adjoint and the
-// temperature lattice converge slowly (thousands of sweeps of a linear
-// iteration), and 11- or 8-bit mantissas accumulate into percent-level errors
-// there, so they stay FP32.
-template <> struct StorageTypes<0> { using T = double; using TG = double; using TA = double; using R = double; };
-template <> struct StorageTypes<1> { using T = float; using TG = float; using TA = float; using R = float; };
-template <> struct StorageTypes<2> { using T = __half; using TG = float; using TA = float; using R = float; };
-template <> struct StorageTypes<3> { using T = __nv_bfloat16; using TG = float; using TA = float; using R = float; };
-
-template <int S>
-FlowArgs<typename StorageTypes<S>::T, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
-flow_args(const FlowLaunch& l) {
-    using T = typename StorageTypes<S>::T;
-    using TA = typename StorageTypes<S>::TA;
-    using R = typename StorageTypes<S>::R;
-    FlowArgs<T, TA, R> a;
-    a.fin = (const T*)l.fin;
-    a.fout = (T*)l.fout;
-    a.ain = (const TA*)l.ain;
-    a.aout = (TA*)l.aout;
-    a.flags = l.flags;
-    a.gamma = (const R*)l.gamma;
-    a.bc = (const R*)l.bc;
-    a.u = (const R*)l.u;
-    a.cpl = (const R*)l.cpl;
-    a.sT = (const R*)l.sT;
-    a.out0 = (R*)l.out0;
-    a.out1 = (R*)l.out1;
-    a.partials = l.partials;
-    a.nx = l.nx;
-    a.ny = l.ny;
-    a.nz = l.nz;
-    a.np = l.np;
-    a.omega = (R)l.omega;
-    a.rho0 = (R)l.rho0;
-    a.src_in = (R)l.src_in;
-    a.ascale = (R)l.ascale;
-    a.model = l.model;
-    return a;
-}
-
-template <int S>
-ThermArgs<typename StorageTypes<S>::TG, typename StorageTypes<S>::TA, typename StorageTypes<S>::R>
-therm_args(const ThermLaunch& l) {
-    using T = typename StorageTypes<S>::TG;
-    using TA = typename StorageTypes<S>::TA;
-    using R = typename StorageTypes<S>::R;
-    ThermArgs<T, TA, R> a;
-    a.gin = (const T*)l.gin;
-    a.gout = (T*)l.gout;
-    a.ain = (const TA*)l.ain;
-    a.aout = (TA*)l.aout;
-    a.flags = l.flags;
-    a.gamma = (const R*)l.gamma;
-    a.bc = (const R*)l.bc;
-    a.u = (const R*)l.u;
-    a.gpost = (const R*)l.gpost;
-    a.gcn = (R*)l.gcn;
-    a.out0 = (R*)l.out0;
-    a.out1 = (R*)l.out1;
-    a.partials = l.partials;
-    a.nx = l.nx;
-    a.ny = l.ny;
-    a.nz = l.nz;
-    a.np = l.np;
-    a.rho0 = (R)l.rho0;
-    a.kappa_f = (R)l.kappa_f;
-    a.k_ratio = (R)l.k_ratio;
-    a.q = (R)l.q;
-    a.T0 = (R)l.T0;
-    a.src_T = (R)l.src_T;
-    a.ascale = (R)l.ascale;
-    a.beta = (R)l.beta;
-    a.src_q = (R)l.src_q;
-    return a;
-}
-
-inline dim3 flat_grid(long long np) { return dim3((unsigned)((np + 255) / 256)); }
-
-// launch a step kernel as a programmatic dependent of the previous kernel in
-// the stream (the kernel waits for it with griddepcontrol.wait)
-template <typename Arg>
-void launch_pdl(void (*kernel)(Arg), const Geom& g, cudaStream_t s, const Arg& a) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = g.grid;
-    cfg.blockDim = g.block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, a);
-}
-
-template <class L, int S>
-void flow_dispatch(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t s) {
-    using T = typename StorageTypes<S>::T;
-    using TA = typename StorageTypes<S>::TA;
-    using R = typename StorageTypes<S>::R;
-    auto a = flow_args<S>(l);
-    switch (op) {
-        case FOP_INIT_F: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
-        case FOP_INIT_A: k_flow_init<L, T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
-        case FOP_STEP: launch_pdl(k_flow_step<L, T, TA, R, false>, g, s, a); break;
-        case FOP_STEP_RED: launch_pdl(k_flow_step<L, T, TA, R, true>, g, s, a); break;
-        case FOP_ADJ: launch_pdl(k_flow_adjoint<L, T, TA, R, false, false>, g, s, a); break;
-        case FOP_ADJ_RED: launch_pdl(k_flow_adjoint<L, T, TA, R, true, false>, g, s, a); break;
-        case FOP_ADJ_T: launch_pdl(k_flow_adjoint<L, T, TA, R, false, true>, g, s, a); break;
-        case FOP_ADJ_T_RED: launch_pdl(k_flow_adjoint<L, T, TA, R, true, true>, g, s, a); break;
-        case FOP_SENS: k_flow_sens<L, T, TA, R, false><<<g.grid, g.block, 0, s>>>(a); break;
-        case FOP_SENS_T: k_flow_sens<L, T, TA, R, true><<<g.grid, g.block, 0, s>>>(a); break;
-    }
-}
-
-template <int S>
-void therm_dispatch(ThermOp op, const ThermLaunch& l, const Geom& g, cudaStream_t s) {
-    using T = typename StorageTypes<S>::TG;
-    using TA = typename StorageTypes<S>::TA;
-    using R = typename StorageTypes<S>::R;
-    auto a = therm_args<S>(l);
-    switch (op) {
-        case TOP_INIT_G: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 0); break;
-        case TOP_INIT_A: k_thermal_init<T, TA, R><<<flat_grid(l.np), 256, 0, s>>>(a, 1); break;
-        case TOP_STEP: launch_pdl(k_thermal_step<T, TA, R, false>, g, s, a); break;
-        case TOP_STEP_RED: launch_pdl(k_thermal_step<T, TA, R, true>, g, s, a); break;
-        case TOP_ADJ: launch_pdl(k_thermal_adjoint<T, TA, R, false>, g, s, a); break;
-        case TOP_ADJ_RED: launch_pdl(k_thermal_adjoint<T, TA, R, true>, g, s, a); break;
-        case TOP_COUPLING: k_thermal_coupling<T, TA, R><<<g.grid, g.block, 0, s>>>(a); break;
-    }
-}
-
 template <typename S, typename D>
 __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, long long n) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -169,34 +31,25 @@ __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, long l
 
 cudaError_t flow_launch(int stencil, int storage, FlowOp op, const FlowLaunch& a, const Geom& g,
                         cudaStream_t s) {
-    if (stencil == 0) {
-        switch (storage) {
-            case 0: flow_dispatch<D2Q9, 0>(op, a, g, s); break;
-            case 1: flow_dispatch<D2Q9, 1>(op, a, g, s); break;
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (storage) {
-            case 0: flow_dispatch<D3Q19, 0>(op, a, g, s); break;
-            case 1: flow_dispatch<D3Q19, 1>(op, a, g, s); break;
-            case 2: flow_dispatch<D3Q19, 2>(op, a, g, s); break;
-            case 3: flow_dispatch<D3Q19, 3>(op, a, g, s); break;
-            default: return cudaErrorInvalidValue;
-        }
+    if (stencil == 0 && storage > 1) return cudaErrorInvalidValue;
+    switch (storage) {
+        case 0: return flow_launch_storage<0>(stencil, op, a, g, s);
+        case 1: return flow_launch_storage<1>(stencil, op, a, g, s);
+        case 2: return flow_launch_storage<2>(stencil, op, a, g, s);
+        case 3: return flow_launch_storage<3>(stencil, op, a, g, s);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t thermal_launch(int storage, ThermOp op, const ThermLaunch& a, const Geom& g,
                            cudaStream_t s) {
     switch (storage) {
-        case 0: therm_dispatch<0>(op, a, g, s); break;
-        case 1: therm_dispatch<1>(op, a, g, s); break;
-        case 2: therm_dispatch<2>(op, a, g, s); break;
-        case 3: therm_dispatch<3>(op, a, g, s); break;
+        case 0: return therm_launch_storage<0>(op, a, g, s);
+        case 1: return therm_launch_storage<1>(op, a, g, s);
+        case 2: return therm_launch_storage<2>(op, a, g, s);
+        case 3: return therm_launch_storage<3>(op, a, g, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 namespace {
@@ -266,6 +119,10 @@ cudaError_t convert_launch(const void* src, int src_f64, void* dst, int dst_f64,
 // argument blocks; one batch per storage type may be live at a time.
 // ---------------------------------------------------------------------------
 namespace {
+using dispatch::StorageTypes;
+using dispatch::flow_args;
+using dispatch::therm_args;
+
 template <int S>
 using BankT = BatchConst<typename StorageTypes<S>::T, typename StorageTypes<S>::TG,
                          typename StorageTypes<S>::TA, typename StorageTypes<S>::R>;

@@ -99,6 +99,7 @@ struct lbm_ctx {
 
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     std::vector<uint8_t> hflags;   // host copy of the flags (per-face boundary values)
+    int mirror = 0;                // axes with symmetry planes (lbm_set_symmetry)
     lbm_batch* holder = nullptr;   // batch whose memory budget counts this context
 
     void drop_graphs() {
@@ -163,6 +164,7 @@ FlowLaunch flow_base(lbm_ctx* c) {
     a.src_in = c->n_in > 0 ? c->obj.w_pin / (3.0 * (double)c->n_in) : 0.0;
     a.ascale = 1.0;
     a.model = c->prm.gamma_model;
+    a.mirror = c->mirror;
     return a;
 }
 
@@ -189,6 +191,7 @@ ThermLaunch therm_base(lbm_ctx* c) {
     a.ascale = 1.0;
     a.beta = c->prm.beta_max;
     a.src_q = c->obj.w_qgen * c->prm.beta_max;
+    a.mirror = c->mirror;
     return a;
 }
 
@@ -665,7 +668,8 @@ lbm_status lbm_set_flags(lbm_ctx* c, const uint8_t* flags, size_t n, int on_devi
         if (type > 3) return fail(LBM_ERR_ARG, "unknown node type at node " + std::to_string(i));
         if ((type >= 2 || (fl & 0x40)) && (code > 5 || (c->stencil == LBM_D2Q9 && code > 3)))
             return fail(LBM_ERR_ARG, "bad normal code at node " + std::to_string(i));
-        if ((fl & 0x40) && type != 1) return fail(LBM_ERR_ARG, "HEAT bit on a non-wall node");
+        if ((fl & 0x40) && type != 1 && type != 3)
+            return fail(LBM_ERR_ARG, "bit 6 on a node that is neither a wall nor a fixed-density node");
         nin += type == 2;
         nnw += type != 1;
     }
@@ -748,6 +752,17 @@ lbm_status lbm_set_objective(lbm_ctx* c, const lbm_objective* o) {
         c->drop_graphs();
     c->obj = *o;
     c->adj_done = c->tadj_done = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_symmetry(lbm_ctx* c, int axes) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    if (axes < 0 || axes > 7) return fail(LBM_ERR_ARG, "axes must be a mask of bits 0 (x), 1 (y), 2 (z)");
+    if (c->stencil == LBM_D2Q9 && (axes & 4)) return fail(LBM_ERR_ARG, "D2Q9 lattices have no z axis");
+    if (axes != c->mirror) c->drop_graphs();  // the captured launches carry the mask
+    c->mirror = axes;
+    c->fwd_done = c->adj_done = false;
+    c->flow_done = c->tadj_done = false;
     return LBM_OK;
 }
 

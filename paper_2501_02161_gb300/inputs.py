@@ -9,11 +9,16 @@ Flag byte per node (the layout the C-ABI documents):
             velocity inlet, Eq. 7), 3 PRES (Zou-He fixed-density outlet, Eq. 8)
   bits 3-5  inward normal of an open boundary or heated wall:
             0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
-  bit 6     HEAT  wall node that injects a heat flux towards its normal
+  bit 6     on a WALL node: HEAT, injects a heat flux towards its normal;
+            on a PRES node: T-inlet, the temperature is held at T_in
+            (a pressure-driven inlet)
   bit 7     reserved (0)
 
 Boundary values, 4 numbers per node (only read at VEL / PRES nodes):
-  VEL:  (ux, uy, uz, T_in)      PRES: (rho_out, 0, 0, 0)
+  VEL:  (ux, uy, uz, T_in)      PRES: (rho, 0, 0, T_in used with bit 6)
+
+Faces of the lattice box are periodic seams unless Lattice.mirror marks an
+axis (bit a) whose two faces are symmetry planes half a node beyond them.
 
 Node linear index n = x + nx*(y + ny*z); arrays are returned flat in that order.
 
@@ -73,6 +78,7 @@ class Lattice:
     w_tmean: float = 0.0       # objective weight of mean temperature
     beta_max: float = 0.0      # heat generation in the solid, Q = beta_max (1-gamma)(1-T) (Eq. 69)
     w_qgen: float = 0.0        # objective weight of J_Q = -sum Q (Eq. 72)
+    mirror: int = 0            # axes with symmetry planes beyond both faces: bit a for axis a
     meta: dict = field(default_factory=dict)
 
     @property
@@ -277,6 +283,87 @@ def heat_sink(nx: int = 128, ny: int = 64, nz: int = 32, umax: float = 0.05,
                   re=re, u_ref=umax, l_ref=float(width), pr=pr)
     lat.meta.update(width=width, umax=umax, re=re, pr=pr, seed=seed)
     return lat
+
+
+def heat_sink_quarter(nx: int = 96, ny: int = 24, nz: int = 12, re: float = 60.0,
+                      u_scale: float = 0.05, pr: float = 7.1, k_ratio: float = 100.0,
+                      beta_max: float = 1e-4, seed: int = 8, sigma: float = 3.0,
+                      plenum: int = 4, T_in: float = 0.0,
+                      gamma_uniform: float | None = None) -> Lattice:
+    """A quarter of a symmetric microchannel heat sink, the setup of the paper's
+    Sec. 3.3 (Fig. 15 is a schematic only): flow along +x driven by a pressure
+    drop between a fixed-density inlet at x=0 (rho_in = rho0 + 3 dp, the
+    temperature held at T_in) and a fixed-density outlet at x=nx-1 (rho0);
+    walls on the outer faces y=ny-1 and z=nz-1; symmetry planes beyond the low
+    y and z faces (the cut planes of the full channel, whose other three
+    quarters are their mirror images; the outer faces reflect too, which the
+    walls there make immaterial); heat generated in the solid,
+    Q = beta_max (1 - gamma)(1 - T), and the objective J = -sum Q (Eq. 72).
+    Re is set through the pressure drop (Eq. 70): dp = rho0 u_scale^2, so the
+    velocity scale is u_scale, with the full channel's smaller open side
+    2 min(ny-1, nz-1) as the length scale."""
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    bc = np.zeros((nz, ny, nx, 4))
+    flags[-1, :, :] = WALL
+    flags[:, -1, :] = WALL
+    dp = u_scale * u_scale          # rho0 = 1
+    inlet = make_flag(PRES, (1, 0, 0), heat=True)   # bit 6 on a PRES node: T held at T_in
+    outlet = make_flag(PRES, (-1, 0, 0))
+    flags[:nz - 1, :ny - 1, 0] = inlet
+    bc[:nz - 1, :ny - 1, 0, :] = (1.0 + 3.0 * dp, 0.0, 0.0, T_in)
+    flags[:nz - 1, :ny - 1, nx - 1] = outlet
+    bc[:nz - 1, :ny - 1, nx - 1, :] = (1.0, 0.0, 0.0, 0.0)
+    if gamma_uniform is not None:
+        gam = np.full((nz, ny, nx), float(gamma_uniform))
+    else:
+        gam = filtered_design((nz, ny, nx), seed, sigma)
+        gam[:, :, :plenum] = 1.0
+        gam[:, :, nx - plenum:] = 1.0
+    kind = flags & 7
+    gam[kind == PRES] = 1.0
+    gam[kind == WALL] = 0.0
+    lat = Lattice(f"heat_sink_quarter_{nx}x{ny}x{nz}", D3Q19, nx, ny, nz, flags.ravel(),
+                  gam.ravel(), bc.ravel(), thermal=True, k_ratio=k_ratio, q_flux=0.0, T0=0.0,
+                  w_pin=0.0, w_tmean=0.0, beta_max=beta_max, w_qgen=1.0,
+                  re=re, u_ref=0.0, dp=dp, l_ref=float(2 * min(ny - 1, nz - 1)), pr=pr,
+                  mirror=(1 << 1) | (1 << 2))
+    lat.meta.update(seed=seed, u_scale=u_scale)
+    return lat
+
+
+def unfold(lat: Lattice, axis: int) -> Lattice:
+    """The lattice doubled across the symmetry plane beyond its low face on
+    `axis` (0 x, 1 y, 2 z): the mirror image of every node, normal and
+    velocity is placed below the original, and the axis becomes periodic (its
+    faces in the doubled lattice are the mirror images of the original's
+    other face).  Solving the unfolded lattice solves the symmetric whole of
+    which `lat` is the part beyond the plane."""
+    bit = 1 << axis
+    if not lat.mirror & bit:
+        raise ValueError("that axis has no symmetry plane")
+    dims = [lat.nz, lat.ny, lat.nx]
+    d = 2 - axis                                     # array dimension of the axis
+    fl = lat.flags.reshape(dims)
+    kind = fl & 7
+    code = (fl >> 3) & 7
+    flip_code = np.where((code >> 1) == axis, code ^ 1, code).astype(np.uint8)
+    has_normal = (kind >= VEL) | ((fl & HEAT_BIT) != 0)
+    fl_m = np.where(has_normal, (fl & 0xC7) | (flip_code << 3), fl).astype(np.uint8)
+    bc = lat.bcval.reshape(dims + [4]).copy()
+    bc_m = bc.copy()
+    bc_m[..., axis] *= np.where(kind == VEL, -1.0, 1.0)
+    g = lat.gamma.reshape(dims)
+    cat = lambda a, b: np.concatenate([np.flip(b, d), a], axis=d)
+    flags2 = cat(fl, fl_m)
+    bc2 = np.concatenate([np.flip(bc_m, d), bc], axis=d)
+    g2 = cat(g, g)
+    nd = list(dims)
+    nd[d] *= 2
+    out = Lattice(**{**lat.__dict__, "name": lat.name + f"_unfolded{'xyz'[axis]}",
+                     "nx": nd[2], "ny": nd[1], "nz": nd[0], "flags": flags2.ravel(),
+                     "gamma": g2.ravel(), "bcval": bc2.ravel(), "mirror": lat.mirror & ~bit,
+                     "meta": dict(lat.meta)})
+    return out
 
 
 def random_fields(lat: Lattice, seed: int, scale: float = 1.0):

@@ -494,13 +494,34 @@ def serve_sequential(requests, storage: str = "fp32", tol: float = 1e-4, max_ste
     return sorted(results, key=lambda r: r.rid)
 
 
-def summarize(results, wall: float | None = None) -> dict:
+RE_BANDS = [(10.0, 20.0), (20.0, 50.0), (50.0, 100.0), (100.0, 200.0), (200.0, 500.0)]
+
+
+def summarize(results, wall: float | None = None, requests=None) -> dict:
+    """Throughput and latency of a served run; with the requests, completed /
+    failed counts per lattice shape and per Re band (failed = diverged, not
+    converged within the step cap counts as completed with its flag, or out
+    of memory)."""
     ok = [r for r in results if r.status >= 0]
     lat = np.array([r.latency for r in results])
     wall = wall if wall is not None else max(r.done for r in results)
-    return {"requests": len(results), "completed": len(ok),
-            "failed": len(results) - len(ok),
-            "sens_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 3),
-            "p50_s": round(float(np.percentile(lat, 50)), 4),
-            "p99_s": round(float(np.percentile(lat, 99)), 4),
-            "mean_s": round(float(lat.mean()), 4)}
+    out = {"requests": len(results), "completed": len(ok),
+           "failed": len(results) - len(ok),
+           "sens_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 3),
+           "p50_s": round(float(np.percentile(lat, 50)), 4),
+           "p99_s": round(float(np.percentile(lat, 99)), 4),
+           "mean_s": round(float(lat.mean()), 4)}
+    if requests is not None:
+        by = {r.rid: r for r in requests}
+        shapes, bands = {}, {}
+        for r in results:
+            q = by[r.rid]
+            sk = "x".join(str(d) for d in q.shape) + ("/thermal" if q.thermal else "")
+            band = next((f"{lo:g}-{hi:g}" for lo, hi in RE_BANDS if lo <= q.re < hi),
+                        f">={RE_BANDS[-1][1]:g}" if q.re >= RE_BANDS[-1][1] else f"<{RE_BANDS[0][0]:g}")
+            for tab, key in ((shapes, sk), (bands, band)):
+                c = tab.setdefault(key, [0, 0])
+                c[0 if r.status >= 0 else 1] += 1
+        out["by_shape"] = {k: {"completed": v[0], "failed": v[1]} for k, v in sorted(shapes.items())}
+        out["by_re"] = {k: {"completed": v[0], "failed": v[1]} for k, v in bands.items()}
+    return out

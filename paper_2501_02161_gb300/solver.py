@@ -70,7 +70,14 @@ class Solver:
         s.set_gamma(torch.as_tensor(lat.gamma, dtype=s.rdtype, device=s.device))
         s.set_bc_values(torch.as_tensor(lat.bcval, dtype=s.rdtype, device=s.device))
         s.set_lattice_params(lat)
+        if getattr(lat, "mirror", 0):
+            s.set_symmetry(lat.mirror)
         return s
+
+    def set_symmetry(self, axes: int):
+        """Symmetry planes beyond both faces of the axes in the mask (bit 0 x,
+        1 y, 2 z) instead of periodic seams."""
+        C.check(self.lib.lbm_set_symmetry(self._ctx, int(axes)), "lbm_set_symmetry")
 
     def set_lattice_params(self, lat):
         """The lattice's physical parameters and objective weights: through

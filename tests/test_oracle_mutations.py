@@ -12,6 +12,7 @@ import pytest
 import test_oracle_continuous as CA
 import test_oracle_heatgen as H
 import test_oracle_pins as T
+import test_oracle_symmetry as SY
 from paper_2501_02161_gb300 import inputs as I
 
 MUTATIONS = {
@@ -25,6 +26,7 @@ MUTATIONS = {
     8: "thermal-to-flow coupling with the wrong sign",
     9: "heat-generation objective source with the wrong sign",
     10: "continuous adjoint boundaries with the printed bottom-outlet / left-inlet indices on every face",
+    11: "symmetry plane that moves the image node but does not reflect the population",
 }
 
 
@@ -44,6 +46,7 @@ def pins(O):
     yield lambda: T.test_sensitivity_vs_finite_difference_2d(O, I.GAMMA_EQ12)
     yield lambda: H.test_sensitivity_with_heat_generation_vs_finite_difference(O)
     yield lambda: CA.test_boundary_term_of_eq25_vanishes_on_every_face(O, (0, -1, 0), I.PRES)
+    yield lambda: SY.test_quarter_equals_the_unfolded_full_domain(O, "qgen")
 
 
 @pytest.mark.parametrize("k", sorted(MUTATIONS), ids=lambda k: MUTATIONS[k])

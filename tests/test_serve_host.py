@@ -260,3 +260,20 @@ def test_a_request_larger_than_the_budget_fails_instead_of_waiting_forever(fakes
         warm = q.kind == "opt" and r.warm
         assert r.status == (C.LBM_ERR_OOM if too_big and not warm else 0), (q.rid, q.shape, r.status)
     assert any(r.status == C.LBM_ERR_OOM for r in res) and any(r.status == 0 for r in res)
+
+
+def test_summary_breaks_failures_down_by_shape_and_re():
+    reqs = [S.Request(0, 0.0, (32, 32, 32), 15.0, False, "sens", 0, 1),
+            S.Request(1, 0.0, (32, 32, 32), 300.0, True, "sens", 1, 2),
+            S.Request(2, 0.0, (64, 64, 64), 60.0, False, "sens", 2, 3),
+            S.Request(3, 0.0, (64, 64, 64), 499.0, False, "sens", 3, 4)]
+    res = [S.Result(0, "sens", 0.0, 0.0, 1.0, status=0), S.Result(1, "sens", 0.0, 0.0, 2.0, status=-4),
+           S.Result(2, "sens", 0.0, 0.0, 3.0, status=1), S.Result(3, "sens", 0.0, 0.0, 4.0, status=-4)]
+    s = S.summarize(res, requests=reqs)
+    assert s["completed"] == 2 and s["failed"] == 2
+    assert s["by_shape"] == {"32x32x32": {"completed": 1, "failed": 0},
+                             "32x32x32/thermal": {"completed": 0, "failed": 1},
+                             "64x64x64": {"completed": 1, "failed": 1}}
+    assert s["by_re"]["10-20"] == {"completed": 1, "failed": 0}
+    assert s["by_re"]["200-500"] == {"completed": 0, "failed": 2}
+    assert s["by_re"]["50-100"] == {"completed": 1, "failed": 0}
