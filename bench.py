@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--nreq-stable", type=int, default=64,
                    help="served requests of the stable-Re stream (0: skip it)")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the level-set and paper heat-sink legs")
     return p.parse_args()
 
 
@@ -606,6 +607,11 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, lats, dev)
 
+    levelset = paper_hs = None
+    if rank == 0 and not args.no_extra:
+        levelset = levelset_leg(dev)
+        paper_hs = paper_heat_sink_leg(dev)
+
     served = None
     if not args.no_serve:
         served = run_serve(args, device=dev)
@@ -635,11 +641,78 @@ def run_ours(args):
                          "MLUPS_if_counted": round((total_ups + total_lost) / (total_ms * 1e-3) / 1e6, 1)},
             "roofline": roof, "roofline_at_workload": at_workload,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "served": served,
+            "levelset": levelset, "paper_heat_sink": paper_hs,
             "gpu_launches": int(total_launch),
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def levelset_leg(dev, iters=6):
+    """The paper's optimiser (Eq. 13-15, 66-67) on the 64 x 64 D2Q9 pipe bend
+    (FP64, tau 0.6, V_max 0.08 pi): per-iteration time of forward + adjoint
+    (warm-started, tolerance 1e-6) + dJ/dgamma + the level-set update."""
+    import torch
+
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.levelset import level_set_loop
+    from paper_2501_02161_gb300.solver import Solver
+
+    lat = I.workload("pipe_bend_2d_64x64")
+    s = Solver.from_lattice(lat, storage="fp64", device=dev)
+    level_set_loop(s, lat, iters=1, K=0.1, sigma=5e-3, vmax=0.08 * math.pi, tol=1e-6,
+                   max_steps=200000, check_every=1000)   # untimed: captures the step graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, hist = level_set_loop(s, lat, iters=iters, K=0.1, sigma=5e-3, vmax=0.08 * math.pi,
+                             tol=1e-6, max_steps=200000, check_every=1000)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"workload": "2D D2Q9 pipe bend 64x64 FP64, level set K 0.1, sigma 5e-3, "
+                        "V_max 0.08 pi, solves to 1e-6 warm-started",
+            "iters": iters, "s_per_iter": round(dt / iters, 4),
+            "J": [round(h["J"], 6) for h in hist],
+            "fluid_fraction": [round(h["fluid_fraction"], 4) for h in hist]}
+
+
+def paper_heat_sink_leg(dev, re_values=(60.0,)):
+    """The paper's heat-sink problem (Sec. 3.3): a quarter domain with
+    symmetry planes, pressure-driven inlet holding T = 0 (Eq. 70), heat
+    generated in the solid (Eq. 69, 71) and J = -sum Q (Eq. 72), Pr 7.1,
+    conductivity ratio 100; forward (flow + temperature) and adjoint to 1e-6
+    in FP32, node updates per second over all phases."""
+    import torch
+
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.solver import Solver
+
+    out = {"workload": "quarter heat sink 192x48x24 (full channel 192x96x48), FP32, tol 1e-6"}
+    for re in re_values:
+        lat = I.heat_sink_quarter(nx=192, ny=48, nz=24, re=re)
+        s = Solver.from_lattice(lat, storage="fp32", device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = {}
+        status = "ok"
+        for ph, name in ((0, "flow"), (1, "temperature"), (3, "temperature_adjoint"), (2, "flow_adjoint")):
+            r = s.solve_phase(ph, tol=1e-6, max_steps=400000, check_every=1000, strict=False)
+            steps[name] = r.steps
+            if r.status < 0:
+                status = "diverged"
+                break
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rec = {"steps": steps, "seconds": round(dt, 3), "status": status,
+               "MLUPS": round(sum(steps.values()) * lat.n / dt / 1e6, 1)}
+        if status == "ok":
+            rec["J_Q"] = s.objective()
+            sens = s.sensitivity(dtype=torch.float64)
+            rec["dJdgamma_abs_max"] = float(sens.abs().max())
+        s.close()
+        out[f"re_{re:g}"] = rec
+    return out
 
 
 def run_e2e(args, lats, dev):

@@ -934,9 +934,26 @@ __device__ __forceinline__ int thermal_pull(const ThermArgs<T, TA, R>& a, const 
     return fl;
 }
 
-// collision with the heat source w_k Q, Q = beta_max (1 - gamma)(1 - T)
-// (Eq. 69, 71); the reducing step also sums T (residual, mean-T objective)
-// and Q (heat-generation objective, Eq. 72) over non-wall nodes
+// temperature collision at a non-wall node with the heat source w_k Q,
+// Q = beta_max (1 - gamma)(1 - T) (Eq. 69, 71), in place; returns Q
+template <typename T, typename TA, typename R>
+__device__ __forceinline__ R thermal_collide(const ThermArgs<T, TA, R>& a, R (&g)[7], R tem, R gam, R u0, R u1,
+                                             R u2) {
+    using X = Ex<R>;
+    const R qs = X::mul(X::mul(a.beta, X::sub(R(1), gam)), X::sub(R(1), tem));
+    const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
+    const R g4 = X::mul(R(4), gam);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const R geq = X::mul(X::mul(R(D3Q7::w(k)), tem), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1)));
+        g[k] = X::fma(R(D3Q7::w(k)), qs, X::fma(om, X::sub(geq, g[k]), g[k]));
+    }
+    return qs;
+}
+
+// one temperature step at a node; the reducing step also sums T (residual,
+// mean-T objective) and Q (heat-generation objective, Eq. 72) over non-wall
+// nodes
 template <typename T, typename TA, typename R, bool REDUCE, bool MIRROR = true>
 __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, const Cell& c, double (&acc)[2]) {
     R g[7], gam, u0, u1, u2;
@@ -951,19 +968,37 @@ __device__ __forceinline__ void thermal_step_node(const ThermArgs<T, TA, R>& a, 
         for (int k = 0; k < 7; ++k) a.out1[(size_t)k * a.np + c.n] = g[k];
     }
     if ((fl & 7) != WALL) {
-        const R qs = X::mul(X::mul(a.beta, X::sub(R(1), gam)), X::sub(R(1), tem));
+        const R qs = thermal_collide(a, g, tem, gam, u0, u1, u2);
         if (REDUCE) {
             acc[0] = (double)tem;
             acc[1] = (double)qs;
         }
-        const R om = R(1) / tau_g<R>(gam, a.kappa_f, a.k_ratio);
-        const R g4 = X::mul(R(4), gam);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const R geq = X::mul(X::mul(R(D3Q7::w(k)), tem), X::fma(g4, ecomp<R>(k, u0, u1, u2), R(1)));
-            g[k] = X::fma(R(D3Q7::w(k)), qs, X::fma(om, X::sub(geq, g[k]), g[k]));
-        }
     }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);
+}
+
+// The temperature lattice starts from g = w T0 (post-boundary state of step
+// 0).  The kernels store post-collision populations, so before the first
+// step that state is collided once, with the frozen flow: unlike the flow's
+// rest equilibrium it is not a fixed point of the collision (advection
+// term, heat source).
+template <typename T, typename TA, typename R>
+__global__ void __launch_bounds__(256) k_thermal_collide_initial(ThermArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    if (!c.active) return;
+    const int fl = a.flags[c.n];
+    if ((fl & 7) == WALL) return;  // no collision at walls: w T0 stays
+    R g[7];
+    using X = Ex<R>;
+    R tem = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        g[k] = X::mul(R(D3Q7::w(k)), a.T0);
+        tem = X::add(tem, g[k]);
+    }
+    thermal_collide(a, g, tem, a.gamma[c.n], a.u[c.n], a.u[a.np + c.n], a.u[2 * a.np + c.n]);
 #pragma unroll
     for (int k = 0; k < 7; ++k)
         Pop<T>::st(a.gout, (size_t)k * a.np + c.n, g[k], R(D3Q7::w(k)) * a.T0);

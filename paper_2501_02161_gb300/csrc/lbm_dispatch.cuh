@@ -164,6 +164,7 @@ void therm_dispatch_m(ThermOp op, const ThermLaunch& l, const Geom& g, cudaStrea
         case TOP_ADJ: launch_pdl(k_thermal_adjoint<T, TA, R, false, M>, g, s, a); break;
         case TOP_ADJ_RED: launch_pdl(k_thermal_adjoint<T, TA, R, true, M>, g, s, a); break;
         case TOP_COUPLING: k_thermal_coupling<T, TA, R, M><<<g.grid, g.block, 0, s>>>(a); break;
+        case TOP_COLLIDE_INIT: k_thermal_collide_initial<T, TA, R><<<g.grid, g.block, 0, s>>>(a); break;
     }
 }
 

@@ -71,7 +71,8 @@ enum FlowOp {
     FOP_SENS_T
 };
 
-enum ThermOp { TOP_INIT_G = 0, TOP_INIT_A, TOP_STEP, TOP_STEP_RED, TOP_ADJ, TOP_ADJ_RED, TOP_COUPLING };
+enum ThermOp { TOP_INIT_G = 0, TOP_INIT_A, TOP_STEP, TOP_STEP_RED, TOP_ADJ, TOP_ADJ_RED, TOP_COUPLING,
+               TOP_COLLIDE_INIT };
 
 // storage codes follow lbm_storage; stencil codes follow lbm_stencil
 cudaError_t flow_launch(int stencil, int storage, FlowOp op, const FlowLaunch& a, const Geom& g,

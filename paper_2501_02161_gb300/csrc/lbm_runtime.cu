@@ -92,6 +92,7 @@ struct lbm_ctx {
     bool have_flags = false, have_gamma = false, have_bc = false, have_params = false;
     bool fwd_done = false, adj_done = false;
     bool flow_done = false, tadj_done = false;  // phase-level completion (lbm_solve_phase)
+    bool g_fresh = false;  // temperature populations hold the initial state, not yet collided
     bool fstate = false, astate = false;  // populations hold a usable (warm-start) state
     double J_p = 0.0, J_T = 0.0, J_Q = 0.0;
     double J() const { return J_p + (thermal ? J_T + J_Q : 0.0); }
@@ -426,6 +427,18 @@ lbm_status init_temperature(lbm_ctx* c) {
     c->gcur = 0;
     CUDA_TRY(thermal_launch(c->storage, TOP_INIT_G, t, c->geom, c->stream));
     c->last_I[PH_THERM] = c->prm.T0;
+    c->g_fresh = true;
+    return LBM_OK;
+}
+
+// the stored temperature populations are post-collision ones: collide the
+// initial state once with the frozen flow before the first temperature step
+lbm_status collide_initial_temperature(lbm_ctx* c) {
+    if (!c->g_fresh) return LBM_OK;
+    ThermLaunch t = therm_base(c);
+    t.gout = c->g[c->gcur];
+    CUDA_TRY(thermal_launch(c->storage, TOP_COLLIDE_INIT, t, c->geom, c->stream));
+    c->g_fresh = false;
     return LBM_OK;
 }
 
@@ -493,6 +506,7 @@ lbm_status solve_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, bool do_rese
     } else if (ph == PH_THERM) {
         if (!c->flow_done) return fail(LBM_ERR_ORDER, "the temperature phase needs a completed flow phase");
         if (do_reset && (st = init_temperature(c)) != LBM_OK) return st;
+        if ((st = collide_initial_temperature(c)) != LBM_OK) return st;
         c->fwd_done = c->tadj_done = c->adj_done = false;
     } else if (ph == PH_TADJ) {
         if (!c->fwd_done) return fail(LBM_ERR_ORDER, "the temperature adjoint needs a completed forward solve");
@@ -1014,7 +1028,7 @@ struct StateHeader {
     int nx, ny, nz;
     long long np, n_in, n_nw;
     int fstate, astate, fwd_done, adj_done;
-    int flow_done, tadj_done;
+    int flow_done, tadj_done, g_fresh;
     double J_p, J_T, J_Q;
     double last_I[4];
     double tau, rho0;
@@ -1082,6 +1096,7 @@ lbm_status lbm_export_state(lbm_ctx* c, void* dst, size_t bytes) {
     h.adj_done = c->adj_done;
     h.flow_done = c->flow_done;
     h.tadj_done = c->tadj_done;
+    h.g_fresh = c->g_fresh;
     h.J_p = c->J_p;
     h.J_T = c->J_T;
     h.J_Q = c->J_Q;
@@ -1130,6 +1145,7 @@ lbm_status lbm_import_state(lbm_ctx* c, const void* src, size_t bytes) {
     c->adj_done = h.adj_done;
     c->flow_done = h.flow_done;
     c->tadj_done = h.tadj_done;
+    c->g_fresh = h.g_fresh;
     c->J_p = h.J_p;
     c->J_T = h.J_T;
     c->J_Q = h.J_Q;
@@ -1338,6 +1354,8 @@ lbm_status batch_advance(lbm_batch* b, int i, int st) {
         if (en.phase == SP_FLOW) {
             c->flow_done = true;
             if (c->thermal) {
+                lbm_status s2 = collide_initial_temperature(c);
+                if (s2 != LBM_OK) return s2;
                 en.phase = SP_THERM;
             } else {
                 c->fwd_done = true;

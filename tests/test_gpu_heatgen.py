@@ -73,3 +73,15 @@ def test_heat_generation_objective_value():
     want = -0.7 * np.sum(0.05 * (1 - lat.gamma[nw]) * (1 - T[nw]))
     assert r.J == pytest.approx(want, rel=1e-12)
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_nonzero_initial_temperature(storage):
+    """The temperature lattice starts from g = w T0; with T0 != 0 that state
+    is not a fixed point of the collision (the advection term moves it), so
+    the first step must collide it like every later state."""
+    lat = I.heat_sink(nx=24, ny=14, nz=10, re=10.0, q_flux=5e-3, seed=4)
+    lat.T0 = 0.3
+    g = run_gpu(lat, storage, 60, 40, K=20)
+    o = run_oracle(lat, 60, 40)
+    compare(g, o, storage)
