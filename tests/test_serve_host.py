@@ -277,3 +277,24 @@ def test_summary_breaks_failures_down_by_shape_and_re():
     assert s["by_re"]["10-20"] == {"completed": 1, "failed": 0}
     assert s["by_re"]["200-500"] == {"completed": 0, "failed": 2}
     assert s["by_re"]["50-100"] == {"completed": 1, "failed": 0}
+
+
+def test_failed_restore_keeps_the_host_budget(fakes):
+    """A design whose state is on the host and that cannot come back (no
+    device room) goes back to the host store: the host budget still holds
+    afterwards (the oldest states are dropped first)."""
+    srv = S.Server("fp32", budget_bytes=1 << 60, check_every=500, max_slots=4, device="cpu",
+                   host_budget_bytes=128)
+    reqs = _reqs(4, seed=3)
+    lat = S.lattice_for(reqs[0])
+    st = torch.zeros(64, dtype=torch.uint8)
+    for d in (100, 101):
+        srv.offloaded[d] = (lat, torch.as_tensor(lat.gamma), torch.zeros(lat.n), st.clone())
+        srv.host_used += 64
+    req = S.Request(99, 0.0, reqs[0].shape, reqs[0].re, reqs[0].thermal, "opt", 100, reqs[0].seed)
+    srv.host_budget = 64            # tightened meanwhile: only one state fits
+    srv._make_room = lambda nb: False
+    assert not srv._admit(req, S.Result(99, "opt", 0.0), 0.0)
+    assert srv.host_used <= srv.host_budget
+    assert 100 in srv.offloaded      # the one that could not come back is the newest entry now
+    srv.close()
