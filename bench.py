@@ -59,25 +59,35 @@ def parse():
     p.add_argument("--cap", type=int, default=CAP,
                    help="step cap per solve phase (lower it only for profiler launch lists)")
     p.add_argument("--mode", default="full", choices=["full", "kernels", "precision", "autograd", "serve", "batchcmp",
-                                                 "levelset"],
+                                                 "levelset", "stability"],
                    help="kernels: time the fused step kernels on a --roof-n lattice; "
-                        "precision: heat sink in FP64/FP32/FP16/BF16 storage, error per field; "
+                        "precision: heat sink in FP32/FP16/BF16 storage, error per field against FP64 "
+                        "at the same per-phase step counts; "
                         "autograd: the filtered / projected gradient loop; serve: the served "
                         "streams; batchcmp: batched vs single-context throughput; levelset: the "
-                        "level-set optimiser on the 2D pipe bend")
+                        "level-set optimiser on the 2D pipe bend; stability: largest stable inlet "
+                        "speed per relaxation time for the forward, discrete and continuous adjoint")
     p.add_argument("--iters", type=int, default=50, help="autograd / levelset modes: optimisation iterations")
     p.add_argument("--nreq", type=int, default=256, help="served requests of the as-specified stream")
     p.add_argument("--nreq-stable", type=int, default=64,
                    help="served requests of the stable-Re stream (0: skip it)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the level-set and paper heat-sink legs")
+    p.add_argument("--stab-steps", type=int, default=1000000, help="stability mode: iterations per run")
+    p.add_argument("--stab-iters", type=int, default=6, help="stability mode: bisection steps")
+    p.add_argument("--stab-umin", type=float, default=0.005)
+    p.add_argument("--stab-umax", type=float, default=0.5)
+    p.add_argument("--stab-taus", type=float, nargs="+", default=[0.52, 0.55, 0.6, 0.8])
     return p.parse_args()
 
 
 def run_precision(args):
-    """128x64x32 heat sink (D3Q19 + D3Q7) solved to 1e-6 in each storage;
-    rel-L2 error of every field against the FP64 run (whose parity with the
-    FP64 oracle the tests establish) and the forward + adjoint MLUPS."""
+    """128x64x32 heat sink (D3Q19 + D3Q7, Re 50): each storage solves every
+    phase (flow, temperature, temperature adjoint, flow adjoint) to 1e-6; an
+    FP64 run then takes exactly the same number of steps of each phase, and
+    the rel-L2 error of every field is taken against it (equal step counts
+    separate rounding from the distance to the fixed point; the FP64 path
+    matches the FP64 oracle to 1e-11 per step and at convergence in the tests)."""
     import numpy as np
     import torch
 
@@ -87,34 +97,46 @@ def run_precision(args):
 
     B.build()
     torch.cuda.set_device(0)
-    out = {"mode": "precision", "workload": "heat sink 128x64x32, Re 50, Pr 7, k_r 100, "
-                                            "forward + adjoint to 1e-6 (temperature lattice included)",
-           "fields": {}}
-    ref = None
-    for storage in ("fp64", "fp32", "fp16", "bf16"):
-        lat = I.heat_sink(re=50.0, seed=4)
+    lat = I.heat_sink(re=50.0, seed=4)
+    phases = ((0, "flow"), (1, "temperature"), (3, "temperature_adjoint"), (2, "flow_adjoint"))
+
+    def solve(storage, steps=None):
         s = Solver.from_lattice(lat, storage=storage, device="cuda:0")
+        got = {}
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rf = s.forward(tol=TOL, max_steps=400000, check_every=CHECK, strict=False)
-        ra = s.adjoint(tol=TOL, max_steps=400000, check_every=CHECK, strict=False) if rf.status >= 0 else None
+        for ph, name in phases:
+            if steps is None:
+                r = s.solve_phase(ph, tol=TOL, max_steps=400000, check_every=CHECK, strict=False)
+            else:
+                r = s.solve_phase(ph, tol=0, max_steps=steps[name], check_every=CHECK, strict=False)
+            got[name] = r.steps
+            if r.status < 0:
+                s.close()
+                return None, got, None
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        rec = {"fwd_steps": rf.steps, "fwd_status": rf.status, "J": rf.J,
-               "adj_steps": ra.steps if ra else 0, "adj_status": ra.status if ra else None,
-               "MLUPS": round((rf.steps + (ra.steps if ra else 0)) * lat.n / dt / 1e6, 1)}
-        if ra is not None and ra.status >= 0:
-            rho, u, T = s.fields(torch.float64)
-            fs, gs = s.adjoint_fields(torch.float64)
-            f = {"rho": rho, "u": u, "T": T, "f*": fs, "g*": gs,
-                 "dJ/dgamma": s.sensitivity(dtype=torch.float64), "J": torch.tensor([rf.J])}
-            f = {k: v.cpu().numpy() for k, v in f.items()}
-            if storage == "fp64":
-                ref = f
-            else:
-                rec["rel_l2_vs_fp64"] = {k: float(np.linalg.norm(f[k] - ref[k]) / np.linalg.norm(ref[k]))
-                                         for k in f}
-        out["fields"][storage] = rec
+        rho, u, T = s.fields(torch.float64)
+        fs, gs = s.adjoint_fields(torch.float64)
+        f = {"rho": rho, "u": u, "T": T, "f*": fs, "g*": gs,
+             "dJ/dgamma": s.sensitivity(dtype=torch.float64), "J": torch.tensor([s.objective()])}
         s.close()
+        return {k: v.cpu().numpy() for k, v in f.items()}, got, dt
+
+    out = {"mode": "precision", "workload": "heat sink 128x64x32, Re 50, Pr 7, k_r 100; every phase "
+                                            "to 1e-6, FP64 reference at the same per-phase step counts",
+           "fields": {}}
+    for storage in ("fp32", "fp16", "bf16"):
+        f, steps, dt = solve(storage)
+        rec = {"steps": steps}
+        if f is None:
+            rec["status"] = "diverged"
+        else:
+            ref, _, _ = solve("fp64", steps)
+            rec["MLUPS"] = round(sum(steps.values()) * lat.n / dt / 1e6, 1)
+            rec["rel_l2_vs_fp64_same_steps"] = {
+                k: float(np.linalg.norm(f[k] - ref[k]) / np.linalg.norm(ref[k])) for k in f}
+        out["fields"][storage] = rec
     print(json.dumps(out))
 
 
@@ -287,6 +309,70 @@ def run_serve(args, nreq=None, device="cuda:0"):
         summ, res = run_all(reqs, False)
         out["stable_re_10_80"] = {"requests": ns, "offline": summ, "accuracy": accuracy(reqs, res)}
     return out
+
+
+def run_stability(args):
+    """The stability test of Sec. 3.1 (Fig. 6) on the CUDA path: the 2D pipe
+    bend's initial geometry (empty chamber, gamma = 1 on the design nodes),
+    for each relaxation time the largest inlet speed u_max at which the run
+    does not diverge within --stab-steps iterations (the paper: 1e6), for the
+    forward LBM, the forward + discrete adjoint and the forward + continuous
+    adjoint.  Bisection on log(u_max) in [--stab-umin, --stab-umax]."""
+    import math
+
+    import torch
+
+    from paper_2501_02161_gb300 import build as B
+    from paper_2501_02161_gb300 import inputs as I
+    from paper_2501_02161_gb300.solver import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    N = args.stab_steps
+    K = 1000
+
+    def stable(tau, umax, scheme):
+        lat = I.pipe_bend_2d(tau=tau, umax=umax, gamma_value=1.0)
+        s = Solver.from_lattice(lat, storage="fp64", device="cuda:0")
+        try:
+            r = s.forward(tol=0, max_steps=N, check_every=K, strict=False)
+            if r.status < 0:
+                return False
+            if scheme is None:
+                return True
+            s.set_adjoint_scheme(scheme)
+            r = s.adjoint(tol=0, max_steps=N, check_every=K, strict=False)
+            return r.status >= 0
+        finally:
+            s.close()
+
+    def limit(tau, scheme, hi_bound=None):
+        lo, hi = math.log(args.stab_umin), math.log(hi_bound or args.stab_umax)
+        if not stable(tau, math.exp(lo), scheme):
+            return 0.0
+        if stable(tau, math.exp(hi), scheme):
+            return math.exp(hi)
+        for _ in range(args.stab_iters):
+            mid = 0.5 * (lo + hi)
+            if stable(tau, math.exp(mid), scheme):
+                lo = mid
+            else:
+                hi = mid
+        return math.exp(lo)
+
+    out = {"mode": "stability", "workload": "2D D2Q9 pipe bend 64x64, gamma = 1 on design nodes, FP64",
+           "iterations": N, "bisection_steps": args.stab_iters, "u_max_range": [args.stab_umin, args.stab_umax],
+           "rows": []}
+    t0 = time.perf_counter()
+    for tau in args.stab_taus:
+        fwd = limit(tau, None)
+        row = {"tau": tau, "forward": round(fwd, 5),
+               "discrete_adjoint": round(limit(tau, "discrete", fwd), 5) if fwd > 0 else 0.0,
+               "continuous_adjoint": round(limit(tau, "continuous", fwd), 5) if fwd > 0 else 0.0}
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    print(json.dumps(out))
 
 
 def run_batchcmp(args):
@@ -848,6 +934,8 @@ if __name__ == "__main__":
         run_levelset(a)
     elif a.mode == "batchcmp":
         run_batchcmp(a)
+    elif a.mode == "stability":
+        run_stability(a)
     elif a.mode == "serve":
         import torch
         torch.cuda.set_device(0)

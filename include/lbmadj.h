@@ -194,6 +194,20 @@ lbm_status lbm_set_physics(lbm_ctx* ctx, const lbm_physics* ph);
  * thermal lattice, give LBM_ERR_ARG. */
 lbm_status lbm_set_objective(lbm_ctx* ctx, const lbm_objective* obj);
 
+/* Which adjoint the flow-adjoint phase iterates.  DISCRETE (default) is the
+ * paper's method (Eq. 53-65: the exact transpose of the forward step).
+ * CONTINUOUS is the comparison the paper argues against (Sec. 2.3, Eq. 23-32):
+ * adjoint collision, backward streaming (Eq. 30), then the boundary rows of
+ * the continuous Lagrangian -- Eq. 27 at fixed-density outlets, Eq. 29 at
+ * velocity inlets, where the objective enters with 2 w_pin / (3 N_in) -- on
+ * any face, bounce-back at walls.  Its dJ/dgamma is Eq. 32 (without lambda)
+ * on its f*; lbm_get_adjoint returns its stored post-collision values C^T f*.
+ * Built for D2Q9 flow lattices without symmetry planes (else
+ * LBM_ERR_UNSUPPORTED, also from lbm_adjoint).  Switching discards the
+ * adjoint state.  Errors: LBM_ERR_ARG (unknown scheme). */
+typedef enum { LBM_ADJOINT_DISCRETE = 0, LBM_ADJOINT_CONTINUOUS = 1 } lbm_adjoint_scheme;
+lbm_status lbm_set_adjoint_scheme(lbm_ctx* ctx, int scheme);
+
 /* Symmetry planes (the quarter-domain heat sink of Sec. 3.3): bit a of axes
  * makes streaming along axis a reflect at both faces of the box instead of
  * wrapping: a pull that leaves the box reads the image node in the plane half

@@ -23,6 +23,7 @@ LBM_FP64, LBM_FP32, LBM_FP16_OFS, LBM_BF16_OFS = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_GAMMA_EQ12, LBM_GAMMA_LINEAR = 0, 1
 LBM_VEL, LBM_PRES = 2, 3
+LBM_ADJOINT_DISCRETE, LBM_ADJOINT_CONTINUOUS = 0, 1
 LBM_PHASE_FLOW, LBM_PHASE_TEMPERATURE, LBM_PHASE_FLOW_ADJOINT, LBM_PHASE_TEMPERATURE_ADJOINT = 0, 1, 2, 3
 
 
@@ -82,6 +83,7 @@ SIGNATURES = {
     "lbm_set_physics": (_I, [_VP, ctypes.POINTER(lbm_physics)]),
     "lbm_set_bc": (_I, [_VP, _I, _I, _VP, _SZ, _I, _I]),
     "lbm_set_symmetry": (_I, [_VP, _I]),
+    "lbm_set_adjoint_scheme": (_I, [_VP, _I]),
     "lbm_forward": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_adjoint": (_I, [_VP, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),
     "lbm_solve_phase": (_I, [_VP, _I, ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_report)]),

@@ -765,6 +765,53 @@ struct AdjMinBlocks {
 
 // THERMAL: the coupling field is present; CPL_RT: decide at run time from
 // whether a coupling field is given (one code path for mixed batches)
+// adjoint collision at a non-wall node, in place (Eq. 63-65): f*_C,i =
+// (1 - 1/tau) f*_S,i + (1/tau) sum_m (d f^eq_m / d f_i) f*_S,m
+// [- dJ/df_i = 1/(3 N_in) at an inlet node when src] [+ thermal coupling]
+template <class L, typename T, typename TA, typename R, bool THERMAL, bool CPL_RT>
+__device__ __forceinline__ void adjoint_collide(const FlowArgs<T, TA, R>& a, long long n, bool src, R (&s)[L::Q]) {
+    using X = Ex<R>;
+    const R g = a.gamma[n];
+    const R u0 = a.u[n], u1 = a.u[a.np + n], u2 = a.u[2 * a.np + n];
+    AdjMoments<L, R> m;
+    m.compute(s);
+    const R Qu0 = X::fma(m.Q02, u2, X::fma(m.Q01, u1, X::mul(m.Q00, u0)));
+    const R Qu1 = X::fma(m.Q12, u2, X::fma(m.Q11, u1, X::mul(m.Q01, u0)));
+    const R Qu2 = X::fma(m.Q22, u2, X::fma(m.Q12, u1, X::mul(m.Q02, u0)));
+    // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
+    const R c1 = X::mul(R(3), g);
+    const R c2 = a.model == 0 ? X::mul(X::mul(R(9), g), g) : X::mul(R(9), g);
+    const R c3 = a.model == 0 ? X::mul(c1, g) : c1;
+    const R c3A = X::mul(c3, m.A);
+    R w0 = X::fma(-c3A, u0, X::fma(c2, Qu0, X::mul(c1, m.M0)));
+    R w1 = X::fma(-c3A, u1, X::fma(c2, Qu1, X::mul(c1, m.M1)));
+    R w2 = X::fma(-c3A, u2, X::fma(c2, Qu2, X::mul(c1, m.M2)));
+    const R om = a.omega;
+    R base = X::mul(om, m.A);
+    if (src) base = X::sub(base, a.src_in);
+    // the coupling term enters through the same fused operation whether
+    // it is present or zero, so every kernel variant rounds alike
+    R v0 = 0, v1 = 0, v2 = 0;
+    if (THERMAL || (CPL_RT && a.cpl != nullptr)) {
+        v0 = a.cpl[n];
+        v1 = a.cpl[a.np + n];
+        v2 = a.cpl[2 * a.np + n];
+    }
+    w0 = X::fma(om, w0, v0);
+    w1 = X::fma(om, w1, v1);
+    w2 = X::fma(om, w2, v2);
+    const R om1 = X::sub(R(1), om);
+    s[0] = X::fma(om1, s[0], base);
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int j = L::opp(i);
+        const R ew = edot_i<L>(i, w0, w1, w2);
+        s[i] = X::fma(om1, s[i], X::add(base, ew));
+        s[j] = X::fma(om1, s[j], X::sub(base, ew));
+    }
+}
+
 template <class L, typename T, typename TA, typename R, bool REDUCE, bool THERMAL, bool CPL_RT = false,
           bool MIRROR = true>
 __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, const Cell& c, double (&acc)[1]) {
@@ -775,46 +822,7 @@ __device__ __forceinline__ void flow_adjoint_node(const FlowArgs<T, TA, R>& a, c
     if (type == WALL) {
         bounce<L>(s);  // C^T = I, B^T = the same swap
     } else {
-        using X = Ex<R>;
-        const R g = a.gamma[c.n];
-        const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
-        AdjMoments<L, R> m;
-        m.compute(s);
-        const R Qu0 = X::fma(m.Q02, u2, X::fma(m.Q01, u1, X::mul(m.Q00, u0)));
-        const R Qu1 = X::fma(m.Q12, u2, X::fma(m.Q11, u1, X::mul(m.Q01, u0)));
-        const R Qu2 = X::fma(m.Q22, u2, X::fma(m.Q12, u1, X::mul(m.Q02, u0)));
-        // sum_m (d f^eq_m / d f_i) f*_m = A + e_i . w
-        const R c1 = X::mul(R(3), g);
-        const R c2 = a.model == 0 ? X::mul(X::mul(R(9), g), g) : X::mul(R(9), g);
-        const R c3 = a.model == 0 ? X::mul(c1, g) : c1;
-        const R c3A = X::mul(c3, m.A);
-        R w0 = X::fma(-c3A, u0, X::fma(c2, Qu0, X::mul(c1, m.M0)));
-        R w1 = X::fma(-c3A, u1, X::fma(c2, Qu1, X::mul(c1, m.M1)));
-        R w2 = X::fma(-c3A, u2, X::fma(c2, Qu2, X::mul(c1, m.M2)));
-        const R om = a.omega;
-        R base = X::mul(om, m.A);
-        if (type == VEL) base = X::sub(base, a.src_in);
-        // the coupling term enters through the same fused operation whether
-        // it is present or zero, so every kernel variant rounds alike
-        R v0 = 0, v1 = 0, v2 = 0;
-        if (THERMAL || (CPL_RT && a.cpl != nullptr)) {
-            v0 = a.cpl[c.n];
-            v1 = a.cpl[a.np + c.n];
-            v2 = a.cpl[2 * a.np + c.n];
-        }
-        w0 = X::fma(om, w0, v0);
-        w1 = X::fma(om, w1, v1);
-        w2 = X::fma(om, w2, v2);
-        const R om1 = X::sub(R(1), om);
-        s[0] = X::fma(om1, s[0], base);
-#pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-            if (L::opp(i) < i) continue;
-            const int j = L::opp(i);
-            const R ew = edot_i<L>(i, w0, w1, w2);
-            s[i] = X::fma(om1, s[i], X::add(base, ew));
-            s[j] = X::fma(om1, s[j], X::sub(base, ew));
-        }
+        adjoint_collide<L, T, TA, R, THERMAL, CPL_RT>(a, c.n, type == VEL, s);
         if (type >= VEL) zou_he_adjoint<L>(s, type, (fl >> 3) & 7);
     }
     const R inv = R(1) / a.ascale;
@@ -867,6 +875,99 @@ __global__ void __launch_bounds__(256) k_flow_sens(FlowArgs<T, TA, R> a) {
     R out = -a.rho0 * a.omega * br;
     if (THERMAL) out += a.sT[c.n];
     a.out0[c.n] = out;
+}
+
+// ---------------------------------------------------------------------------
+// the continuous adjoint LBM (Sec. 2.3), the comparison the paper draws:
+// collide (C^T, no source), stream backwards, then the boundary rows derived
+// from the continuous Lagrangian (Eq. 27 fixed-density outlet, Eq. 29
+// velocity inlet, where the objective enters) and bounce-back at walls.  The
+// kernels store c = C^T f* (the post-collision adjoint); a step pulls
+// c(x + e_i), applies the boundary rows at the node (the result is f*, whose
+// mean sum |f*| the residual uses) and collides.  At an open node with
+// inward normal n the values with e_k.n < 0 came through the periodic wrap:
+//   outlet: f*_k = f*_opp(k) - 12 sum_{e_i.n > 0} w_i f*_i
+//   inlet:  f*_k = f*_opp(k) - 2 w_pin / (3 N_in)
+// which is Eq. 27 (bottom outlet) and Eq. 29 (left inlet) on every face.
+// ---------------------------------------------------------------------------
+template <class L, typename R>
+__device__ __forceinline__ void cont_boundary(R (&s)[L::Q], int fl, R s_in) {
+    using X = Ex<R>;
+    const int type = fl & 7;
+    if (type == WALL) {
+        bounce<L>(s);
+        return;
+    }
+    if (type < VEL) return;
+    const int code = (fl >> 3) & 7;
+    const int ax = code >> 1;
+    const int sg = (code & 1) ? -1 : 1;
+    const int n0 = ax == 0 ? sg : 0, n1 = ax == 1 ? sg : 0, n2 = ax == 2 ? sg : 0;
+    R sub = s_in;
+    if (type == PRES) {
+        sub = R(0);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            if (L::cx(i) * n0 + L::cy(i) * n1 + L::cz(i) * n2 > 0) sub = X::fma(R(12.0 * L::w(i)), s[i], sub);
+    }
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k)
+        if (L::cx(k) * n0 + L::cy(k) * n1 + L::cz(k) * n2 < 0) s[k] = X::sub(s[L::opp(k)], sub);
+}
+
+template <class L, typename T, typename TA, typename R, bool REDUCE>
+__global__ void __launch_bounds__(256) k_flow_adjoint_cont(FlowArgs<T, TA, R> a) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const Cell c = this_cell(a.nx, a.ny);
+    double acc[1] = {0.0};
+    if (c.active) {
+        R s[L::Q];
+        pull_adjoint<L, false>(a, c, s);
+        const int fl = a.flags[c.n];
+        const int type = fl & 7;
+        cont_boundary<L>(s, fl, Ex<R>::mul(R(2), a.src_in));
+        if (REDUCE && type != WALL) {
+            R t = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) t = Ex<R>::add(t, fabs(s[i]));
+            acc[0] = (double)t;
+        }
+        if (type != WALL) adjoint_collide<L, T, TA, R, false, false>(a, c.n, false, s);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) Pop<TA>::st(a.aout, (size_t)i * a.np + c.n, s[i], R(0));
+    }
+    if (REDUCE) block_partials<1>(acc, a.partials, grid_block_id());
+}
+
+// J'(x) = -(1/tau) sum_i f*_i d f^eq_i / d gamma with the continuous adjoint
+// f* of the last step (Eq. 32 without lambda); zero at walls
+template <class L, typename T, typename TA, typename R>
+__global__ void __launch_bounds__(256) k_flow_sens_cont(FlowArgs<T, TA, R> a) {
+    const Cell c = this_cell(a.nx, a.ny);
+    if (!c.active) return;
+    const int fl = a.flags[c.n];
+    if ((fl & 7) == WALL) {
+        a.out0[c.n] = R(0);
+        return;
+    }
+    R s[L::Q];
+    pull_adjoint<L, false>(a, c, s);
+    cont_boundary<L>(s, fl, Ex<R>::mul(R(2), a.src_in));
+    const R g = a.gamma[c.n];
+    const R u0 = a.u[c.n], u1 = a.u[a.np + c.n], u2 = a.u[2 * a.np + c.n];
+    AdjMoments<L, R> m;
+    m.compute(s);
+    const R Mu = m.M0 * u0 + m.M1 * u1 + m.M2 * u2;
+    const R uQu = m.Q00 * u0 * u0 + m.Q11 * u1 * u1 + m.Q22 * u2 * u2 +
+                  R(2) * (m.Q01 * u0 * u1 + m.Q02 * u0 * u2 + m.Q12 * u1 * u2);
+    const R uu = u0 * u0 + u1 * u1 + u2 * u2;
+    R br;
+    if (a.model == 0)
+        br = R(3) * Mu + R(9) * g * uQu - R(3) * g * uu * m.A;
+    else
+        br = R(3) * Mu + R(4.5) * uQu - R(1.5) * uu * m.A;
+    a.out0[c.n] = -a.rho0 * a.omega * br;
 }
 
 // ---------------------------------------------------------------------------

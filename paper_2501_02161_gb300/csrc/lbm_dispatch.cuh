@@ -138,6 +138,19 @@ void flow_dispatch_m(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t
         case FOP_ADJ_T_RED: launch_pdl(k_flow_adjoint<L, T, TA, R, true, true, M>, g, s, a); break;
         case FOP_SENS: k_flow_sens<L, T, TA, R, false, M><<<g.grid, g.block, 0, s>>>(a); break;
         case FOP_SENS_T: k_flow_sens<L, T, TA, R, true, M><<<g.grid, g.block, 0, s>>>(a); break;
+        case FOP_ADJ_CONT:
+        case FOP_ADJ_CONT_RED:
+        case FOP_SENS_CONT:
+            // the continuous adjoint is built for D2Q9 without symmetry planes
+            if constexpr (L::Q == 9 && !M) {
+                if (op == FOP_ADJ_CONT)
+                    launch_pdl(k_flow_adjoint_cont<L, T, TA, R, false>, g, s, a);
+                else if (op == FOP_ADJ_CONT_RED)
+                    launch_pdl(k_flow_adjoint_cont<L, T, TA, R, true>, g, s, a);
+                else
+                    k_flow_sens_cont<L, T, TA, R><<<g.grid, g.block, 0, s>>>(a);
+            }
+            break;
     }
 }
 

@@ -68,7 +68,10 @@ enum FlowOp {
     FOP_ADJ_T,
     FOP_ADJ_T_RED,
     FOP_SENS,
-    FOP_SENS_T
+    FOP_SENS_T,
+    FOP_ADJ_CONT,      // continuous adjoint step (D2Q9 / D3Q19, no symmetry planes)
+    FOP_ADJ_CONT_RED,
+    FOP_SENS_CONT
 };
 
 enum ThermOp { TOP_INIT_G = 0, TOP_INIT_A, TOP_STEP, TOP_STEP_RED, TOP_ADJ, TOP_ADJ_RED, TOP_COUPLING,

@@ -101,6 +101,7 @@ struct lbm_ctx {
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     std::vector<uint8_t> hflags;   // host copy of the flags (per-face boundary values)
     int mirror = 0;                // axes with symmetry planes (lbm_set_symmetry)
+    int adj_scheme = LBM_ADJOINT_DISCRETE;  // lbm_set_adjoint_scheme
     lbm_batch* holder = nullptr;   // batch whose memory budget counts this context
 
     void drop_graphs() {
@@ -225,6 +226,7 @@ cudaError_t enqueue_step(lbm_ctx* c, int ph, bool reduce, cudaStream_t s) {
         a.ain = c->fa[c->facur];
         a.aout = c->fa[1 - c->facur];
         FlowOp op = c->thermal ? (reduce ? FOP_ADJ_T_RED : FOP_ADJ_T) : (reduce ? FOP_ADJ_RED : FOP_ADJ);
+        if (c->adj_scheme == LBM_ADJOINT_CONTINUOUS) op = reduce ? FOP_ADJ_CONT_RED : FOP_ADJ_CONT;
         e = flow_launch(c->stencil, c->storage, op, a, c->geom, s);
         c->facur ^= 1;
     } else {
@@ -517,6 +519,9 @@ lbm_status solve_phase(lbm_ctx* c, int ph, const lbm_solve_opts* o, bool do_rese
         c->tadj_done = c->adj_done = false;
     } else {
         if (!c->fwd_done) return fail(LBM_ERR_ORDER, "the flow adjoint needs a completed forward solve");
+        if (c->adj_scheme == LBM_ADJOINT_CONTINUOUS && (c->stencil != LBM_D2Q9 || c->thermal || c->mirror))
+            return fail(LBM_ERR_UNSUPPORTED,
+                        "the continuous adjoint is built for D2Q9 flow without symmetry planes");
         if (c->thermal && !c->tadj_done)
             return fail(LBM_ERR_ORDER, "the flow adjoint needs a completed temperature adjoint");
         if (!c->astate) {
@@ -769,6 +774,21 @@ lbm_status lbm_set_objective(lbm_ctx* c, const lbm_objective* o) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_adjoint_scheme(lbm_ctx* c, int scheme) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is null");
+    if (scheme != LBM_ADJOINT_DISCRETE && scheme != LBM_ADJOINT_CONTINUOUS)
+        return fail(LBM_ERR_ARG, "unknown adjoint scheme");
+    if (scheme == LBM_ADJOINT_CONTINUOUS && (c->stencil != LBM_D2Q9 || c->thermal))
+        return fail(LBM_ERR_UNSUPPORTED, "the continuous adjoint is built for D2Q9 flow lattices");
+    if (scheme != c->adj_scheme) {
+        c->drop_graphs();
+        c->astate = false;  // the stored adjoint means another quantity
+    }
+    c->adj_scheme = scheme;
+    c->adj_done = c->tadj_done = false;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_symmetry(lbm_ctx* c, int axes) {
     if (!c) return fail(LBM_ERR_ARG, "ctx is null");
     if (axes < 0 || axes > 7) return fail(LBM_ERR_ARG, "axes must be a mask of bits 0 (x), 1 (y), 2 (z)");
@@ -973,7 +993,8 @@ lbm_status lbm_sensitivity(lbm_ctx* c, void* out, int dtype, int on_device) {
     FlowLaunch a = flow_base(c);
     a.ain = c->fa[c->facur];
     a.out0 = c->sens;
-    CUDA_TRY(flow_launch(c->stencil, c->storage, c->thermal ? FOP_SENS_T : FOP_SENS, a, c->geom, c->stream));
+    const FlowOp op = c->adj_scheme == LBM_ADJOINT_CONTINUOUS ? FOP_SENS_CONT : (c->thermal ? FOP_SENS_T : FOP_SENS);
+    CUDA_TRY(flow_launch(c->stencil, c->storage, op, a, c->geom, c->stream));
     st = copy_out(c, out, c->sens, 1, dtype, on_device);
     if (st != LBM_OK) return st;
     return leave(c);

@@ -74,6 +74,12 @@ class Solver:
             s.set_symmetry(lat.mirror)
         return s
 
+    def set_adjoint_scheme(self, scheme: str):
+        """'discrete' (the paper's method, default) or 'continuous' (the
+        comparison of Sec. 2.3; D2Q9 flow lattices)."""
+        code = {"discrete": C.LBM_ADJOINT_DISCRETE, "continuous": C.LBM_ADJOINT_CONTINUOUS}[scheme]
+        C.check(self.lib.lbm_set_adjoint_scheme(self._ctx, code), "lbm_set_adjoint_scheme")
+
     def set_symmetry(self, axes: int):
         """Symmetry planes beyond both faces of the axes in the mask (bit 0 x,
         1 y, 2 z) instead of periodic seams."""
