@@ -200,8 +200,11 @@ lbm_status lbm_set_objective(lbm_ctx* ctx, const lbm_objective* obj);
  * adjoint collision, backward streaming (Eq. 30), then the boundary rows of
  * the continuous Lagrangian -- Eq. 27 at fixed-density outlets, Eq. 29 at
  * velocity inlets, where the objective enters with 2 w_pin / (3 N_in) -- on
- * any face, bounce-back at walls.  Its dJ/dgamma is Eq. 32 (without lambda)
- * on its f*; lbm_get_adjoint returns its stored post-collision values C^T f*.
+ * any face, bounce-back at walls.  It stores the post-collision values
+ * C^T f* (what lbm_get_adjoint returns); its dJ/dgamma is Eq. 32 (without
+ * lambda) on the f* those values give, the boundary rows applied to the
+ * backward-streamed store: the iterate one step after the last step counted
+ * (the same f* once converged).
  * Built for D2Q9 flow lattices without symmetry planes (else
  * LBM_ERR_UNSUPPORTED, also from lbm_adjoint).  Switching discards the
  * adjoint state.  Errors: LBM_ERR_ARG (unknown scheme). */

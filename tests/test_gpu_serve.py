@@ -195,3 +195,25 @@ def test_largest_served_shape_matches_oracle(solo_tiles):
         assert errs[k] <= 1e-5, errs
     for k in ("sens", "fs", "gs"):
         assert errs[k] <= 1e-4, errs
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("solo_tiles", [0, 1], ids=["packed", "solo"])
+def test_paper_heat_sink_in_the_batch_equals_single_context(storage, solo_tiles):
+    """The paper's heat-sink problem (quarter domain with symmetry planes,
+    pressure-driven inlet holding T, heat generation, J_Q) served in the
+    batch beside other lattices, packed and solo: bit-identical to the
+    single-context solve."""
+    from paper_2501_02161_gb300.solver import Solver
+    q = I.heat_sink_quarter(nx=32, ny=10, nz=8, re=20.0, beta_max=0.01, plenum=3, seed=3)
+    lats = [q, I.pipe_bend_3d(n=24, width=6, re=20.0, seed=2)]
+    got = solve_batched(lats, storage=storage, solo_tiles=solo_tiles)
+    rep, sens, u = got[0]
+    s = Solver.from_lattice(q, storage=storage)
+    rf = s.forward(tol=1e-5, max_steps=20000, check_every=K)
+    ra = s.adjoint(tol=1e-5, max_steps=20000, check_every=K)
+    assert rep.status >= 0 and rep.steps == rf.steps + ra.steps
+    assert torch.equal(s.sensitivity(dtype=torch.float64).cpu(), sens)
+    assert torch.equal(s.fields(torch.float64)[1].cpu(), u)
+    assert rep.J == rf.J
+    s.close()
