@@ -498,10 +498,11 @@ RE_BANDS = [(10.0, 20.0), (20.0, 50.0), (50.0, 100.0), (100.0, 200.0), (200.0, 5
 
 
 def summarize(results, wall: float | None = None, requests=None) -> dict:
-    """Throughput and latency of a served run; with the requests, completed /
-    failed counts per lattice shape and per Re band (failed = diverged, not
-    converged within the step cap counts as completed with its flag, or out
-    of memory)."""
+    """Throughput and latency of a served run: the count of results per status
+    (LBM_OK, LBM_NOT_CONVERGED within the step cap, LBM_ERR_DIVERGED,
+    LBM_ERR_OOM) and, with the requests, completed / failed counts per
+    lattice shape and per Re band (failed = an error status; a result not
+    converged within the step cap counts as completed with its flag)."""
     ok = [r for r in results if r.status >= 0]
     lat = np.array([r.latency for r in results])
     wall = wall if wall is not None else max(r.done for r in results)
@@ -511,6 +512,11 @@ def summarize(results, wall: float | None = None, requests=None) -> dict:
            "p50_s": round(float(np.percentile(lat, 50)), 4),
            "p99_s": round(float(np.percentile(lat, 99)), 4),
            "mean_s": round(float(lat.mean()), 4)}
+    by_status = {}
+    for r in results:
+        name = C.STATUS_NAMES.get(r.status, str(r.status))
+        by_status[name] = by_status.get(name, 0) + 1
+    out["by_status"] = dict(sorted(by_status.items()))
     if requests is not None:
         by = {r.rid: r for r in requests}
         shapes, bands = {}, {}

@@ -277,6 +277,7 @@ def test_summary_breaks_failures_down_by_shape_and_re():
     assert s["by_re"]["10-20"] == {"completed": 1, "failed": 0}
     assert s["by_re"]["200-500"] == {"completed": 0, "failed": 2}
     assert s["by_re"]["50-100"] == {"completed": 1, "failed": 0}
+    assert s["by_status"] == {"LBM_ERR_DIVERGED": 2, "LBM_NOT_CONVERGED": 1, "LBM_OK": 1}
 
 
 def test_failed_restore_keeps_the_host_budget(fakes):
