@@ -37,9 +37,9 @@ ADJ_BYTES = {"fp32": 19 * 4 * 2 + 12 + 4 + 1, "fp64": 19 * 8 * 2 + 24 + 8 + 1,
 THERM_BYTES = 7 * 4 * 2 + 12 + 4 + 1   # D3Q7 FP32 populations + frozen u + gamma + flag
 # DRAM bytes per node per launch (dram__bytes_read.sum + dram__bytes_write.sum
 # / nodes) from one ncu capture of the current kernels on a 160^3 pipe bend
-# (profiles/k_flow_*_pipe_bend_160cubed_fp32.md); traffic grows with the node
+# (FP32 forward and adjoint, FP16 paired forward); traffic grows with the node
 # count, so a launch on N nodes moves N times this.
-TRAFFIC_B_PER_NODE = {("adjoint", "fp32"): 156.8, ("forward", "fp32"): 145.4}
+TRAFFIC_B_PER_NODE = {("adjoint", "fp32"): 156.9, ("forward", "fp32"): 145.5, ("forward", "fp16"): 70.9}
 
 
 def parse():

@@ -51,12 +51,14 @@ def test_sixteen_bit_error_vs_oracle(lat, storage):
 
 @pytest.mark.parametrize("storage,pdt,code", [("fp16", torch.float16, 2), ("bf16", torch.bfloat16, 3)])
 @pytest.mark.parametrize("shape", [(16, 12, 10), (24, 9, 7), (2, 5, 3)])
-def test_paired_sixteen_bit_step_is_bit_identical_to_the_one_node_step(storage, pdt, code, shape):
+@pytest.mark.parametrize("model", [0, 1])
+def test_paired_sixteen_bit_step_is_bit_identical_to_the_one_node_step(storage, pdt, code, shape, model):
     """The plain 16-bit forward step runs two x-adjacent nodes per thread; the
     reducing step and the allocation-free entry point run one node per thread.
     From the same random populations on a periodic box (every pull wraps at
     some node; walls, an inlet and an outlet on the x faces), N context steps
-    (N - 1 paired + one reducing) and N one-node steps give the same bits."""
+    (N - 1 paired + one reducing) and N one-node steps give the same bits.
+    Both gamma models."""
     import ctypes
     from paper_2501_02161_gb300 import _capi as C
     from paper_2501_02161_gb300.solver import Solver
@@ -71,14 +73,14 @@ def test_paired_sixteen_bit_step_is_bit_identical_to_the_one_node_step(storage, 
     bc[:, :, 0, 0] = 0.02
     bc[:, :, nx - 1, 0] = 1.0
     lat = I.Lattice("box", I.D3Q19, nx, ny, nz, flags.ravel(), 0.3 + 0.7 * rng.random(N), bc.ravel(),
-                    tau=0.7)
+                    tau=0.7, gamma_model=model)
     s = Solver.from_lattice(lat, storage=storage)
     s.forward(tol=0, max_steps=2, check_every=2)
     st = s.export_state()
     hdr = 256
     np_ = (N + 63) // 64 * 64
     f0 = (0.01 * torch.randn(19 * np_, dtype=torch.float32)).to(pdt)
-    st[hdr:hdr + 2 * 19 * np_] = f0.view(torch.uint8)
+    st[hdr:hdr + f0.element_size() * 19 * np_] = f0.view(torch.uint8)
     s.import_state(st)
     steps = 6
     s.forward(tol=0, max_steps=steps, check_every=steps, reset=False)
@@ -96,7 +98,7 @@ def test_paired_sixteen_bit_step_is_bit_identical_to_the_one_node_step(storage, 
     for k in range(steps):
         d = C.lbm_step_desc(C.LBM_D3Q19, code, nx, ny, nz, np_, f[k % 2].data_ptr(),
                             f[(k + 1) % 2].data_ptr(), fl.data_ptr(), g.data_ptr(), b.data_ptr(),
-                            rho2.data_ptr(), u2.data_ptr(), sums.data_ptr(), 0.7, 1.0, 0)
+                            rho2.data_ptr(), u2.data_ptr(), sums.data_ptr(), 0.7, 1.0, model)
         C.check(C.lib().lbm_flow_step_noalloc(ctypes.byref(d), ctypes.c_void_p(stream)), "noalloc")
     torch.cuda.synchronize()
     assert torch.equal(rho.cpu(), rho2.cpu())
