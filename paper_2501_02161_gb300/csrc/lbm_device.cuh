@@ -664,16 +664,17 @@ template <> struct Pair16<__nv_bfloat16> {
     }
 };
 
-// resident 256-thread blocks per SM for the paired step: 4 (64 registers, a
-// few bytes spilled) measured 3 % faster than 3 (80 registers, no spill) and
-// 5 % faster than 2 at 320^3, where the kernel is issue-bound
-template <class L, typename T>
-struct PairMinBlocks {
-    static constexpr int value = 4;
+// block size and resident blocks per SM of the paired step (64 registers,
+// a few bytes spilled).  Measured at 320^3, where the kernel is issue-bound:
+// 128 x 8 moved 0.872 of the HBM copy rate (FP16), 256 x 4 0.838, 64 x 16
+// 0.798, 512 x 2 0.769; 256 x 3 (80 registers, no spill) was 3 % slower than
+// 256 x 4
+struct PairShape {
+    static constexpr int threads = 128, blocks = 8;
 };
 
 template <class L, typename T, typename TA, typename R>
-__global__ void __launch_bounds__(256, (PairMinBlocks<L, T>::value)) k_flow_step_pair(FlowArgs<T, TA, R> a) {
+__global__ void __launch_bounds__(PairShape::threads, PairShape::blocks) k_flow_step_pair(FlowArgs<T, TA, R> a) {
     pdl_launch_dependents();
     pdl_wait();
     const int px = blockIdx.x * blockDim.x + threadIdx.x;

@@ -125,7 +125,8 @@ void flow_dispatch_m(FlowOp op, const FlowLaunch& l, const Geom& g, cudaStream_t
             // nodes per thread
             if constexpr (sizeof(T) == 2 && L::Q == 19 && !M) {
                 if ((l.nx % 2) == 0) {
-                    launch_pdl(k_flow_step_pair<L, T, TA, R>, make_geom(l.nx / 2, l.ny, l.nz), s, a);
+                    launch_pdl(k_flow_step_pair<L, T, TA, R>,
+                               make_geom(l.nx / 2, l.ny, l.nz, PairShape::threads), s, a);
                     break;
                 }
             }

@@ -13,9 +13,10 @@ struct Geom {
     long long nblocks;  // grid.x * grid.y * grid.z (reduction partial count)
 };
 
-// (BX x BY) tiles of x-y planes, one thread per node, 256 threads when the
-// lattice is wide enough; BX divides nx when possible so no lane idles.
-Geom make_geom(int nx, int ny, int nz);
+// (BX x BY) tiles of x-y planes, one thread per node, `threads` per block
+// when the lattice is wide enough; BX divides nx when possible so no lane
+// idles.
+Geom make_geom(int nx, int ny, int nz, int threads = 256);
 
 struct FlowLaunch {
     const void* fin;

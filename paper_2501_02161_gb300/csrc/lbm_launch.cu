@@ -7,10 +7,11 @@
 
 namespace lbm {
 
-Geom make_geom(int nx, int ny, int nz) {
+Geom make_geom(int nx, int ny, int nz, int threads) {
     Geom g;
     int bx = (nx % 128 == 0) ? 128 : ((nx % 64 == 0 || nx > 96) ? 64 : 32);
-    int by = 256 / bx;
+    if (bx > threads) bx = threads;
+    int by = threads / bx;
     if (by > ny) by = ny;
     if (by < 1) by = 1;
     g.block = dim3(bx, by, 1);
