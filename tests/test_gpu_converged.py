@@ -10,8 +10,10 @@ step counts separate FP32 rounding from the distance to the fixed point
 iterations between them, not by rounding).  Bounds are the workload's:
 rel-L2 <= 1e-5 on rho, u, T and J, <= 1e-4 on dJ/dgamma, f* and g*.
 
-The full-size 128x64x32 heat sink (tens of thousands of steps per phase,
-about an hour of FP64 oracle time) runs only with LBM_LONG_TESTS=1.
+The 64^3 pipe bend at Re 100 and the full-size 128x64x32 heat sink run only
+with LBM_LONG_TESTS=1: the oracle replays every step in FP64 (the heat sink,
+tens of thousands of steps per phase through explicit-Jacobian adjoints,
+takes more than 45 minutes on 16 cores).
 """
 import json
 import os
