@@ -613,7 +613,8 @@ __device__ __forceinline__ void flow_step_node(const FlowArgs<T, TA, R>& a, cons
 // resident 256-thread blocks per SM asked of the compiler for the forward
 // step: with 16-bit populations 6 (40 registers, a few spilled bytes) beat 5
 // (48) by 4 % at 320^3, where the kernel is issue-bound; FP32 keeps 5 (48
-// registers, no spills; 6 blocks were 5 % slower at 64^3)
+// registers, no spills; 6 blocks, 40 registers and 20 spilled bytes, were
+// 3 % slower at both 64^3 and 320^3)
 template <class L, typename T>
 struct FwdMinBlocks {
     static constexpr int value = L::Q != 19 ? 1 : (sizeof(T) == 2 ? 6 : (sizeof(T) == 4 ? 5 : 1));
