@@ -69,6 +69,7 @@ def parse():
                         "speed per relaxation time for the forward, discrete and continuous adjoint")
     p.add_argument("--iters", type=int, default=50, help="autograd / levelset modes: optimisation iterations")
     p.add_argument("--nreq", type=int, default=256, help="served requests of the as-specified stream")
+    p.add_argument("--cases", default="", help="batchcmp: run only the cases whose name contains this")
     p.add_argument("--fp16-tol-factor", type=float, default=0.25,
                    help="serving: the 16-bit path's extra run uses this times the tolerance")
     p.add_argument("--nreq-stable", type=int, default=64,
@@ -446,6 +447,8 @@ def run_batchcmp(args):
                I.pipe_bend_3d(n=192, ny=96, nz=48, width=12, re=20.0)], 4000)]
     out = {"mode": "batchcmp", "storage": "fp32", "steps": "forward N + adjoint N per lattice"}
     for name, lats, steps in cases:
+        if args.cases and args.cases not in name:
+            continue
         nodes = sum(l.n for l in lats)
         ts, tb, tp = single(lats, steps), batched(lats, steps), batched(lats, steps, 0)
         out[name] = {"single_MLUPS": round(2 * nodes * steps / ts / 1e6, 1),
