@@ -445,6 +445,8 @@ def run_batchcmp(args):
              ("1 x 64^3", [I.pipe_bend_3d(n=64, re=20.0)], 10000),
              ("4 x 64^3", [I.pipe_bend_3d(n=64, re=20.0, seed=k) for k in range(4)], 4000),
              ("16 x 32^3", [I.pipe_bend_3d(n=32, re=20.0, seed=k) for k in range(16)], 4000),
+             ("32 x 32^3", [I.pipe_bend_3d(n=32, re=20.0, seed=k) for k in range(32)], 2000),
+             ("32 x 16^3", [I.pipe_bend_3d(n=16, width=4, re=10.0, seed=k) for k in range(32)], 4000),
              ("mix 32^3+64^3+96x48x24+128x64x32+192x96x48",
               [I.pipe_bend_3d(n=32, re=20.0), I.pipe_bend_3d(n=64, re=20.0),
                I.pipe_bend_3d(n=96, ny=48, nz=24, width=12, re=20.0),
@@ -456,9 +458,11 @@ def run_batchcmp(args):
             continue
         nodes = sum(l.n for l in lats)
         ts, tb, tp = single(lats, steps), batched(lats, steps), batched(lats, steps, 0)
+        t1 = batched(lats, steps, 1)   # every lattice on its own graph and stream
         out[name] = {"single_MLUPS": round(2 * nodes * steps / ts / 1e6, 1),
                      "batched_MLUPS": round(2 * nodes * steps / tb / 1e6, 1),
-                     "packed_only_MLUPS": round(2 * nodes * steps / tp / 1e6, 1)}
+                     "packed_only_MLUPS": round(2 * nodes * steps / tp / 1e6, 1),
+                     "solo_only_MLUPS": round(2 * nodes * steps / t1 / 1e6, 1)}
     print(json.dumps(out))
 
 

@@ -343,12 +343,12 @@ lbm_status lbm_import_state(lbm_ctx* ctx, const void* src, size_t bytes);
  * lbm_adjoint do (same step counts, same FP64 sums), so a context's results
  * are bit-identical alone, in any mix, and through the single-context calls.
  * Contexts may be admitted and retired between steps (continuous batching);
- * admission never re-captures the graph.  A lattice large enough to fill the
- * GPU on its own (by default: at least one wave of the persistent launch,
- * see lbm_batch_set_solo_tiles) runs its K steps as its own single-lattice
- * graph on its context's stream, concurrently with the packed launch; its
- * results are those of the single-context calls by construction.  Built for
- * D3Q19 with FP32, FP16_OFS or BF16_OFS storage.
+ * admission never re-captures the graph.  A lattice at or above the solo
+ * threshold (lbm_batch_set_solo_tiles; by default every lattice) runs its K
+ * steps as its own single-lattice graph on its context's stream, all of them
+ * concurrently and beside the packed launch; its results are those of the
+ * single-context calls by construction.  Built for D3Q19 with FP32, FP16_OFS
+ * or BF16_OFS storage.
  * --------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
@@ -391,9 +391,10 @@ lbm_status lbm_batch_admit(lbm_batch* b, lbm_ctx* ctx, const lbm_solve_opts* opt
 lbm_status lbm_batch_step(lbm_batch* b, int* n_active);
 
 /* Contexts admitted from now on whose lattice has at least min_tiles tiles
- * (256-node blocks of its single-lattice launch) run solo; 0 packs every
- * lattice into the persistent launch.  The default is the persistent launch's
- * resident block count (SMs x blocks per SM).  Errors: LBM_ERR_ARG. */
+ * (256-node blocks of its single-lattice launch) run solo; the others are
+ * packed into the persistent launch; 0 packs every lattice.  The default is
+ * 1: every lattice solo (concurrent single-lattice graphs measured faster
+ * than the packed launch for every mix tried).  Errors: LBM_ERR_ARG. */
 lbm_status lbm_batch_set_solo_tiles(lbm_batch* b, long long min_tiles);
 
 /* Contexts that finished since the last poll: up to max (slot, context,

@@ -151,7 +151,8 @@ class Batch:
                  solo_tiles: int | None = None, budget_bytes: int = 0):
         """solo_tiles: lattices with at least this many 256-node tiles run their
         own single-lattice graph beside the packed launch (0: pack every
-        lattice; None: the library's default, one wave of the packed launch).
+        lattice; None: the library's default, 1: every lattice on its own
+        graph and stream).
         budget_bytes: device memory the batch's contexts may hold together,
         admitted or kept for a warm start (0: no limit); the library counts it."""
         self.lib = C.lib()

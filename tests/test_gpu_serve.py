@@ -54,9 +54,9 @@ def solve_batched(lats, storage="fp32", tol=1e-5, max_steps=20000, order=None, s
     return out
 
 
-# solo_tiles: None = library default (these lattices are all packed), 0 = all
-# packed, 1 = every lattice on its own graph, 40 = some of each
-@pytest.mark.parametrize("solo_tiles", [None, 1, 40])
+# solo_tiles: None = library default (every lattice on its own graph), 0 = all
+# packed into the persistent launch, 40 = some of each
+@pytest.mark.parametrize("solo_tiles", [None, 0, 40])
 def test_batched_equals_single_context_bitwise(solo_tiles):
     from paper_2501_02161_gb300.solver import Solver
     lats = mix()
@@ -149,7 +149,7 @@ def test_tight_budget_offloads_designs_and_still_matches_sequential():
 @pytest.mark.parametrize("solo_tiles", [None, 0], ids=["solo", "packed"])
 def test_largest_served_shape_matches_oracle(solo_tiles):
     """The largest served lattice (192 x 96 x 48 heat sink, flow + temperature)
-    through the batch, on its own graph (solo, the default at this size) and
+    through the batch, on its own graph (solo, the default) and
     inside the packed persistent launch, against the FP64 oracle after the same
     fixed number of steps of every phase: every node compared, FP32 tolerances
     (rel-L2 1e-5 on rho, u, T, J; 1e-4 on f*, g*, dJ/dgamma)."""
