@@ -1236,7 +1236,7 @@ struct BatchEntry {
     int status = LBM_OK;     // worst warning / first error
     double t0 = 0;
     bool used = false;
-    bool solo = false;       // runs its own single-lattice graph (large lattice)
+    bool solo = false;       // runs its own single-lattice graph (at or above the solo threshold)
 };
 
 }  // namespace

@@ -5,9 +5,11 @@ them, in arrival order, as batch slots and HBM budget free up (admission by
 the device footprint each context needs), keeps finished designs resident so
 that an optimisation-step request on the same design warm-starts from its
 populations, and advances every resident lattice together: one
-`lbm_batch_step` is one CUDA-graph replay of persistent kernels covering all
-resident lattices for K steps.  Lattices that arrive while others run join at
-the next replay.  The baseline serves the same requests one at a time through
+`lbm_batch_step` runs K steps of every resident lattice, each on its own
+CUDA graph and stream by default (all concurrently), or, below a chosen tile
+threshold, packed into one graph of persistent kernels that walk the tiles
+of all packed lattices.  Lattices that arrive while others run join at the
+next step.  The baseline serves the same requests one at a time through
 the plain single-context FP32 path.  All solver work runs in the CUDA library;
 this module only schedules.
 """
