@@ -337,18 +337,18 @@ lbm_status lbm_import_state(lbm_ctx* ctx, const void* src, size_t bytes);
  *
  * A batch advances many resident contexts together: every call of
  * lbm_batch_step runs check_every steps of each admitted context's current
- * phase (flow, temperature, temperature adjoint, flow adjoint) as one CUDA
- * graph replay of persistent kernels that walk the tiles of all resident
- * lattices, then checks each context's residual exactly as lbm_forward /
- * lbm_adjoint do (same step counts, same FP64 sums), so a context's results
- * are bit-identical alone, in any mix, and through the single-context calls.
- * Contexts may be admitted and retired between steps (continuous batching);
- * admission never re-captures the graph.  A lattice at or above the solo
- * threshold (lbm_batch_set_solo_tiles; by default every lattice) runs its K
- * steps as its own single-lattice graph on its context's stream, all of them
- * concurrently and beside the packed launch; its results are those of the
- * single-context calls by construction.  Built for D3Q19 with FP32, FP16_OFS
- * or BF16_OFS storage.
+ * phase (flow, temperature, temperature adjoint, flow adjoint), then checks
+ * each context's residual exactly as lbm_forward / lbm_adjoint do (same step
+ * counts, same FP64 sums), so a context's results are bit-identical alone, in
+ * any mix, and through the single-context calls.  A lattice at or above the
+ * solo threshold (lbm_batch_set_solo_tiles; by default every lattice) runs its
+ * K steps as its own single-lattice graph on its context's stream, all of
+ * them concurrently; lattices below it are packed into one CUDA graph replay
+ * of persistent kernels that walk the tiles of all packed lattices (each tile
+ * one block of that lattice's single-lattice launch).  Contexts may be
+ * admitted and retired between steps (continuous batching); admission never
+ * re-captures the packed graph.  Built for D3Q19 with FP32, FP16_OFS or
+ * BF16_OFS storage.
  * --------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
